@@ -1,0 +1,289 @@
+"""Benchmark of batched pose evaluation: docked ligands/s and pose-evals/s on GB300.
+
+Workload: 1,024 synthetic ligands (16-64 atoms, 2-12 rotatable bonds) x one
+64^3 pocket at 0.5 Å; 64 initial poses, 10 degree step, 4 repetitions, bump
+threshold 2.0 Å, nearest-voxel score, FP32. A step docks the whole batch
+(every (ligand, pose) through the full greedy sweep, best pose per ligand).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line. Under torchrun each rank docks its own 1,024 ligands
+(weak scaling, no collective on the data path); rank 0 prints the line.
+--impl reference times the FP64 CPU oracle (the reference arm) on the host.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "docked ligands/s & pose-evals/s, batched vs plain, 1 GB300, score err <=1e-4 rel"
+UNIT = "ligands/s"
+WORKLOAD = "batched: 1024 ligands (16-64 atoms, 2-12 rotatable bonds) x 1 pocket 64^3 @0.5A, 64 poses, 10 deg, 4 reps"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = [r.split(",") for r in self.out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def workload(rank=0):
+    import synth.configs as C
+    pks, batch, kn = C.batched()
+    if rank:
+        # weak scaling: every rank docks its own 1,024 ligands of the same distribution
+        import synth
+        l, t = synth.ligand_sizes(1, 1024, 0, [16, 64, 2, 12], id0=1024 * rank)
+        batch = synth.ligand_batch(1, l, t, id0=1024 * rank)
+    return pks[0], batch, kn
+
+
+def input_bytes(batch):
+    return sum(a.nbytes for a in (batch.atom_off, batch.xyz, batch.bond_off, batch.bonds, batch.rot_off, batch.rot))
+
+
+def cpu_baseline(pk, batch, kn, target_s=12.0):
+    """The FP64 oracle as it stands, on the host cores, over a bounded sample of the workload's ligands."""
+    import oracle
+    opk = oracle.OraclePocket(pk)
+    cores = os.cpu_count() or 1
+    done, elapsed, start = 0, 0.0, 0
+    chunk = 2 * cores
+    while elapsed < target_s and start < batch.n:
+        idx = np.arange(start, min(start + chunk, batch.n))
+        sub = batch.subset(idx)
+        t0 = time.perf_counter()
+        oracle.dock(opk, sub, kn, nthreads=cores, ids=idx + batch.id_base)
+        elapsed += time.perf_counter() - t0
+        done += len(idx)
+        start += len(idx)
+    return {"value": done / elapsed, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {done} of the {batch.n} workload ligands, all 64 poses each ({elapsed:.1f} s)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    pk, batch, kn = workload(0)
+    import oracle
+    opk = oracle.OraclePocket(pk)
+    cores = os.cpu_count() or 1
+    per_step = 2 * cores
+    for w in range(args.warmup):
+        idx = np.arange(w * per_step % batch.n, w * per_step % batch.n + per_step) % batch.n
+        oracle.dock(opk, batch.subset(idx), kn, nthreads=cores, ids=idx)
+    times, n = [], 0
+    for s in range(args.steps):
+        idx = np.arange((args.warmup + s) * per_step, (args.warmup + s + 1) * per_step) % batch.n
+        sub = batch.subset(idx)
+        t0 = time.perf_counter()
+        oracle.dock(opk, sub, kn, nthreads=cores, ids=idx)
+        times.append(time.perf_counter() - t0)
+        n += len(idx)
+    tot = sum(times)
+    value = n / tot
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "step_sample": f"{per_step} ligands per step on the host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} workload ligands per step, {args.steps} steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1901_06363_gb300 import Docker
+
+    pk, batch, kn = workload(rank)
+    n, natoms = batch.n, int(batch.atom_off[-1])
+    dk = Docker(local)
+    pid = dk.init_pocket(pk)
+    bid = dk.upload_ligands(batch)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    out = torch.zeros(n * 4, dtype=torch.int32, device=dev)
+    xyz = torch.zeros(natoms * 3, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # larger than the 129 MB L2
+
+    def step():
+        dk.run(bid, [pid], kn, n, natoms, out=out, xyz_out=xyz, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sweep_ms = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()  # L2 flushed between timed steps (outside the events)
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+            sweep_ms.append(dk.stats()["sweep_ms"])
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+        dist.barrier()
+    st = dk.stats()
+    cand_per_step = st["candidates"]
+    value = world * n * args.steps / total_s
+
+    # end to end through the C ABI with host buffers: upload (H2D), dock, results back (D2H)
+    e2e_steps = max(2, min(args.steps, 5))
+    res_host = None
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        b2 = dk.upload_ligands(batch)
+        res_host, xyz_host = dk.run(b2, [pid], kn, n, natoms)
+        dk.release_batch(b2)
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * n * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": input_bytes(batch),
+           "d2h_bytes_per_step": int(res_host.nbytes + xyz_host.nbytes)}
+
+    # plain per-ligand form (one launch per pair, no graph), one step
+    torch.cuda.synchronize()
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dk.run(bid, [pid], dict(kn, plain_mode=1), n, natoms, out=out, xyz_out=xyz, stream=stream)  # warm
+    torch.cuda.synchronize()
+    pe0.record(stream)
+    dk.run(bid, [pid], dict(kn, plain_mode=1), n, natoms, out=out, xyz_out=xyz, stream=stream)
+    pe1.record(stream)
+    torch.cuda.synchronize()
+    plain_s = pe0.elapsed_time(pe1) / 1e3
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks, src = _peaks()
+    f_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    # issue-slot roofline of the sweep kernel: 4 schedulers x 32 lanes per SM per clock
+    peak_inst = sms * 4 * 32 * f_mhz * 1e6 / 1e12
+    # algorithmic instructions per launch: 16 per (candidate, moving atom) field lookup
+    # (6 FMA rotation, 3 floor, 3 bound tests, 2 index, 1 load, 1 add) and 8 per circle
+    # bound test of the bump check (3 sub, 3 FMA, compare, vote)
+    inst = 16.0 * st["atom_updates"] + 8.0 * st["pair_bounds"]
+    sweep_avg = statistics.mean(sweep_ms)
+    achieved = inst / (sweep_avg / 1e3) / 1e12
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "ligands_per_gpu": n, "poses": kn["n_poses"], "step_deg": kn["hp_step"],
+                   "repetitions": kn["repetitions"], "grid": list(pk.dims), "score": "nearest",
+                   "l2": "flushed between timed steps (256 MiB write)"},
+        "pose_evals_per_s": world * cand_per_step * args.steps / total_s,
+        "atoms_per_s": world * natoms * args.steps / total_s,
+        "plain_ligands_per_s": world * n / plain_s,
+        "batched_vs_plain": (value / world) / (n / plain_s),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_inst, "unit": "Tinst/s",
+                     "frac": achieved / peak_inst, "traffic": None,
+                     "kernel": "sweep_kernel", "sweep_ms": sweep_avg,
+                     "peak_source": f"152 SMs x 128 lanes x sm_max_mhz {f_mhz:.0f} ({src} clocks)"},
+        "cpu_baseline": cpu_baseline(pk, batch, kn) if world == 1 else None,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": int(st["kernel_launches"]) * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,271 @@
+/*
+ * geodock.h - C ABI of the GB300 batched pose evaluator for the geometric
+ * docking kernel of GeoDock-MA (Gadioli et al., "Tunable Approximations to
+ * Control Time-to-Solution in an HPC Molecular Docking Mini-App").
+ *
+ * For every (pocket, ligand, initial pose) the library runs the greedy
+ * torsion sweep of Alg. 1/Alg. 2: for each rotamer, the left and then the
+ * right fragment is rotated through its candidate angles, every candidate is
+ * checked for internal bumps and scored with the overlap score of Eq. 1, and
+ * the fragment is set to the best angle found. The knobs of Sec. 3.3
+ * (high/low precision step, threshold, repetitions, tile peeling) are run-time
+ * parameters, as are the number of seeded rigid initial orientations and pose
+ * clipping. All work runs in CUDA kernels for sm_103a; there is no CPU path.
+ *
+ * Conventions
+ *  - Every call returns 0 (DOCK_OK) or a negative DOCK_ERR_* code; the text of
+ *    the last error of a context is returned by dock_last_error().
+ *  - The library copies every input it is given and keeps no caller pointer.
+ *  - Outputs go to caller-owned buffers. Host buffers are written before the
+ *    call returns; device buffers are written in stream order on `stream`.
+ *  - A context is thread-compatible, not thread-safe: one thread at a time.
+ *  - Per-pair status flags (e.g. "every initial pose was outside the box")
+ *    are results, not errors.
+ *
+ * Units: coordinates in Å, angles in degrees. Internally the path works in
+ * grid units of the pocket (Å / h) in FP32; grid values are exact integers.
+ */
+#ifndef GEODOCK_H
+#define GEODOCK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DOCK_OK 0
+#define DOCK_ERR_INVALID_ARG (-1)   /* a size, pointer, index or knob out of range */
+#define DOCK_ERR_TOPOLOGY (-2)      /* a rotatable bond does not split its ligand in two */
+#define DOCK_ERR_OUT_OF_MEMORY (-3) /* a device allocation failed */
+#define DOCK_ERR_CUDA (-4)          /* a CUDA runtime call failed (text in dock_last_error) */
+#define DOCK_ERR_TIMEOUT (-5)       /* a bounded device-side wait gave up */
+#define DOCK_ERR_UNSUPPORTED (-6)   /* a knob combination this build does not run */
+
+/* largest ligand (atoms) and the largest grid edge (voxels) */
+#define DOCK_MAX_ATOMS 255
+#define DOCK_MAX_GRID 256
+#define DOCK_MAX_POSES 4096
+
+typedef struct dock_ctx dock_ctx;
+
+/* A pocket: probe points on voxel centres and the grid that tabulates them.
+ * Eq. 1 takes, for each ligand atom, the minimum squared distance to the
+ * pocket's points (Sec. 3.1: the PASS probe-sphere centres). The library
+ * tabulates that minimum on the voxel centres in grid units,
+ *   K(v) = max(min_j |v - p_j|^2, 1),
+ * an exact integer (the floor at one voxel spacing squared keeps Eq. 1's
+ * denominator positive).
+ *   nx, ny, nz  grid size, 2..DOCK_MAX_GRID each
+ *   h           voxel edge (Å), > 0
+ *   origin      position of voxel (0,0,0)'s centre (Å)
+ *   centre      pocket centre (Å); initial poses put the ligand centroid here
+ *   K           optional host array nx*ny*nz (x fastest) used as the field as
+ *               is (values >= 1); NULL: the field is built on the GPU from pts
+ *   pts         host array 3*npts of voxel indices (x, y, z) inside the grid
+ *   npts        >= 1 unless K is given */
+typedef struct {
+    int nx, ny, nz;
+    double h;
+    double origin[3];
+    double centre[3];
+    const uint16_t* K;
+    const int32_t* pts;
+    int npts;
+} dock_pocket;
+
+/* A batch of ligands in CSR form, host arrays (Sec. 2: atoms, covalent bonds
+ * and the rotamers among them).
+ *   n          number of ligands (>= 0)
+ *   atom_off   n+1 offsets; ligand b owns atoms [atom_off[b], atom_off[b+1]),
+ *              1..DOCK_MAX_ATOMS of them
+ *   xyz        3*atom_off[n] floats, x y z per atom (Å)
+ *   bond_off   n+1 offsets into bonds
+ *   bonds      2*bond_off[n] ligand-local atom indices (u, v)
+ *   rot_off    n+1 offsets into rot
+ *   rot        ligand-local bond indices of the rotatable bonds, in sweep
+ *              order; each must split its ligand into two fragments
+ *   id_base    ligand id of ligand 0 (seeds its initial orientations)
+ *   ids        optional n ids (overrides id_base + b) */
+typedef struct {
+    int n;
+    const int32_t* atom_off;
+    const float* xyz;
+    const int32_t* bond_off;
+    const int32_t* bonds;
+    const int32_t* rot_off;
+    const int32_t* rot;
+    int64_t id_base;
+    const int64_t* ids;
+} dock_ligand_batch;
+
+/* Knobs (Sec. 3.3 and Alg. 2, plus the poses and pose clipping).
+ *   hp_step, lp_step   high/low precision angle steps, degrees in [1, 360];
+ *                      a sweep tries angles k*step < 360, k >= 1
+ *   threshold          fragments with (atoms in fragment / atoms in ligand)
+ *                      <= threshold take lp_step, others hp_step
+ *   repetitions        passes of the whole greedy procedure, >= 0
+ *   n_poses            rigid initial orientations, 1..DOCK_MAX_POSES; pose 0
+ *                      is the input conformer, the others are seeded uniform
+ *                      random rotations about the centroid (SplitMix64 +
+ *                      Shoemake quaternions)
+ *   enable_refinement  tile peeling of Alg. 2 / Eq. 2-3 for hp fragments
+ *   clip_box           1: a candidate with a moving atom outside the grid is
+ *                      infeasible and an initial pose with an atom outside is
+ *                      skipped; 0: lookups clamp to the box and add the
+ *                      squared distance outside it
+ *   bump_thr           Å; a candidate is infeasible when an atom pair whose
+ *                      distance depends on the torsion is closer than this
+ *   score_mode         0 nearest voxel, 1 trilinear interpolation of K
+ *   refine_steps       0; gradient refinement is a separate call
+ *   seed               seed of the initial orientations
+ *   plain_mode         1: one launch per (pocket, ligand) pair, no bucketing
+ *                      and no graph (the comparison form); 0: batched */
+typedef struct {
+    double hp_step, lp_step, threshold;
+    int repetitions, n_poses;
+    int enable_refinement;
+    int clip_box;
+    double bump_thr;
+    int score_mode;
+    int refine_steps;
+    uint64_t seed;
+    int plain_mode;
+} dock_knobs;
+
+/* One (pocket, ligand) result.
+ *   score   best overlap score o = l / sum_i D_i (Eq. 1, Å^-2) over the
+ *           initial poses after the sweep; 0 when status != 0
+ *   pose    index of the initial pose that reached it (ties: lowest), -1
+ *   status  0 ok, 1 every initial pose was skipped (outside the box) */
+typedef struct {
+    float score;
+    int32_t pose;
+    int32_t status;
+    int32_t reserved;
+} dock_result;
+
+/* Create a context on CUDA device `device`; *out receives it. */
+int dock_create(dock_ctx** out, int device);
+
+/* Release every device buffer and the context itself. NULL is ignored. */
+void dock_destroy(dock_ctx* ctx);
+
+/* Text of the last error on this context ("" when none). Owned by ctx. */
+const char* dock_last_error(const dock_ctx* ctx);
+
+/* Upload a pocket and build its field K on the GPU (Eq. 1, inner minimum),
+ * unless p->K is given. *pocket_id receives its handle. Synchronous. */
+int dock_init_pocket(dock_ctx* ctx, const dock_pocket* p, int* pocket_id);
+
+/* Copy a pocket's field back to host memory K (nx*ny*nz uint16, x fastest). */
+int dock_pocket_field(dock_ctx* ctx, int pocket_id, uint16_t* K);
+
+/* Upload a ligand batch: checks the topology, finds the two fragments of
+ * every rotatable bond (Alg. 1: "grow the right and left fragment", the left
+ * one holding the bond's lower atom index) and copies atoms and fragment
+ * tables to the GPU. *batch_id receives its handle. Synchronous.
+ * Errors: DOCK_ERR_INVALID_ARG (sizes, indices), DOCK_ERR_TOPOLOGY. */
+int dock_upload_ligands(dock_ctx* ctx, const dock_ligand_batch* b, int* batch_id);
+
+/* Free a batch's device memory. */
+int dock_release_batch(dock_ctx* ctx, int batch_id);
+
+/* Dock every ligand of the batch into every listed pocket (Alg. 2 per
+ * (pocket, ligand, initial pose); best pose per pair).
+ *   pocket_ids, npockets   host array of pocket handles (>= 1)
+ *   k                      knobs
+ *   out                    npockets*n results, pocket-major (caller-owned)
+ *   xyz_out                NULL, or npockets*3*atom_off[n] floats: the best
+ *                          pose's coordinates (Å) per pair, pocket-major
+ *   out_on_device          0: out/xyz_out are host memory and the call waits
+ *                          for the results; 1: device memory, written in
+ *                          stream order and the call returns at once
+ *   stream                 cudaStream_t to run on (NULL: the legacy stream)
+ * Device memory for the run is allocated by the library on first use and
+ * reused; the batched form replays a CUDA graph per (batch, knobs, pockets). */
+int dock_run(dock_ctx* ctx, int batch_id, const int32_t* pocket_ids, int npockets, const dock_knobs* k,
+             dock_result* out, float* xyz_out, int out_on_device, void* stream);
+
+/* Per-candidate trace of one run on one pocket, for parity checks against a
+ * reference implementation. Every pointer is device memory (nullable except
+ * chosen_k). Sweep index of (ligand b, pose p, sweep s):
+ *     sweep_base[b] + p * nsweep[b] + s,  nsweep[b] = repetitions * 2 * T_b,
+ *     sweep_base[b] = n_poses * sum_{b' < b} nsweep[b'],
+ * sweeps ordered repetition, rotatable bond, then left before right.
+ * Candidate slot j of a sweep is at sweep_index * pmax + j; slot 0 is the
+ * incumbent (angle 0), slot k >= 1 the angle k*step of a flat sweep; with tile
+ * peeling slots 1..360/x are the tile centres and the next x/step slots the
+ * angles of the best tile.
+ *   chosen_k     committed slot per sweep
+ *   cand_S       S = sum_i D_i in grid units per slot (o = l / (h^2 S))
+ *   cand_status  1 feasible, 0 bump, -1 outside box, -2 slot not evaluated
+ *   pose_S       final S per (ligand, pose) (b * n_poses + p); pose_status
+ *                0 ok, 1 skipped; pose_init_S initial S
+ *   init_xyz, pose_xyz  per (ligand, pose) coordinates (Å) at
+ *                (atom_off[b] * n_poses + p * l_b) * 3 */
+typedef struct {
+    int32_t pmax;
+    const int64_t* sweep_base;
+    int32_t* chosen_k;
+    float* cand_S;
+    int32_t* cand_status;
+    float* pose_S;
+    float* pose_init_S;
+    int32_t* pose_status;
+    float* init_xyz;
+    float* pose_xyz;
+} dock_trace;
+
+/* dock_run on one pocket with the trace above recorded (same kernels, trace
+ * stores switched on). Synchronous. */
+int dock_run_trace(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs* k, const dock_trace* tr,
+                   dock_result* out, void* stream);
+
+/* Candidate slots per sweep of the trace layout for these knobs. */
+int dock_trace_pmax(const dock_knobs* k);
+
+/* Tile shape of the sweep kernel. lanes_per_pose (1, 2, 4, 8) lanes share a
+ * pose and split its angles; angles_per_chunk (8, 12, 18, 36) angles a lane
+ * keeps in registers; warps_per_cta. dock_set_tile forces a shape for the
+ * batched form (0 fields keep the current choice); dock_autotune times the
+ * shapes on a sample of the batch and keeps the fastest for (batch, knobs). */
+typedef struct {
+    int lanes_per_pose;
+    int angles_per_chunk;
+    int warps_per_cta;
+} dock_tile;
+
+int dock_set_tile(dock_ctx* ctx, const dock_tile* t);
+int dock_get_tile(const dock_ctx* ctx, dock_tile* t);
+int dock_autotune(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs* k, dock_tile* best, void* stream);
+
+/* Work and timing of the last dock_run, counted from the topology and knobs:
+ *   candidates       candidate angles evaluated, over all (pocket, ligand,
+ *                    pose, sweep), excluding the incumbents
+ *   atom_updates     (candidate, moving atom) pairs: each is one rotation and
+ *                    one field lookup
+ *   pair_bounds      (sweep, angle chunk, moving atom, partner atom) circle
+ *                    bound tests of the bump check
+ *   bump_pairs       (candidate, atom pair) distance tests a bump check
+ *                    without the circle bound would make
+ *   kernel_launches  CUDA kernels launched by the call
+ *   sweep_ms         device time of the sweep kernel(s) of the call, from
+ *                    CUDA events recorded around them on the call's stream
+ *                    (waits for the call to finish) */
+typedef struct {
+    uint64_t candidates;
+    uint64_t atom_updates;
+    uint64_t pair_bounds;
+    uint64_t bump_pairs;
+    uint64_t kernel_launches;
+    double sweep_ms;
+} dock_stats;
+
+int dock_last_stats(const dock_ctx* ctx, dock_stats* s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GEODOCK_H */

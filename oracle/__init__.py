@@ -59,6 +59,7 @@ class Knobs(ctypes.Structure):
 class Out(ctypes.Structure):
     _fields_ = [("best_score", P(ctypes.c_double)), ("best_pose", P(ctypes.c_int32)), ("status", P(ctypes.c_int32)),
                 ("pose_S", P(ctypes.c_double)), ("pose_init_S", P(ctypes.c_double)),
+                ("pose_init_lo", P(ctypes.c_double)), ("pose_init_hi", P(ctypes.c_double)),
                 ("pose_status", P(ctypes.c_int32)), ("pose_xyz", P(ctypes.c_double)),
                 ("init_xyz", P(ctypes.c_double)), ("sweep_base", P(ctypes.c_int64)), ("force_k", P(ctypes.c_int32)),
                 ("chosen_k", P(ctypes.c_int32)), ("own_k", P(ctypes.c_int32)), ("pmax", ctypes.c_int32),
@@ -210,13 +211,14 @@ def dock(opk: OraclePocket, batch, kn, trace=False, force_k=None, amb_delta=0.0,
     res = {
         "best_score": np.zeros(n, np.float64), "best_pose": np.zeros(n, np.int32), "status": np.zeros(n, np.int32),
         "pose_S": np.zeros(n * N, np.float64), "pose_init_S": np.zeros(n * N, np.float64),
+        "pose_init_lo": np.zeros(n * N, np.float64), "pose_init_hi": np.zeros(n * N, np.float64),
         "pose_status": np.zeros(n * N, np.int32),
     }
     if xyz_out:
         res["pose_xyz"] = np.zeros(natoms * N * 3, np.float64)
         res["init_xyz"] = np.zeros(natoms * N * 3, np.float64)
     o = Out()
-    for k in ("best_score", "pose_S", "pose_init_S", "pose_xyz", "init_xyz"):
+    for k in ("best_score", "pose_S", "pose_init_S", "pose_init_lo", "pose_init_hi", "pose_xyz", "init_xyz"):
         if k in res:
             setattr(o, k, _ptr(res[k], ctypes.c_double))
     for k in ("best_pose", "status", "pose_status"):

@@ -102,6 +102,8 @@ struct or_out {
     // per (ligand, pose): index atom-independent = pose_base[b] + p
     double* pose_S;        // final S, grid units (0 when skipped)
     double* pose_init_S;   // initial S
+    double* pose_init_lo;  // its interval over voxel-boundary alternatives (nullable)
+    double* pose_init_hi;
     int32_t* pose_status;  // 0 ok, 1 skipped
     double* pose_xyz;      // final coordinates, Å, (atom_off[b]*N + p*l_b)*3 (nullable)
     double* init_xyz;      // initial coordinates, same layout (nullable)
@@ -523,9 +525,11 @@ void dock_ligand(const Ctx& C, int b) {
             for (int i = 0; i < m.l; ++i)
                 for (int a = 0; a < 3; ++a) O.init_xyz[xo + 3 * i + a] = x[i][a];
         bool clip = K.clip_box != 0;
-        Score s0 = score_all(C.G, K.score_mode, x, clip, 0.0);
+        Score s0 = score_all(C.G, K.score_mode, x, clip, K.amb_delta);
         double S_cur = s0.S;
         if (O.pose_init_S) O.pose_init_S[pose_base + p] = S_cur;
+        if (O.pose_init_lo) O.pose_init_lo[pose_base + p] = s0.lo;
+        if (O.pose_init_hi) O.pose_init_hi[pose_base + p] = s0.hi;
         bool skipped = !topo_ok || (clip && !s0.inbox);
         if (O.pose_status) O.pose_status[pose_base + p] = skipped ? 1 : 0;
         if (skipped) {

@@ -1,0 +1,292 @@
+"""ctypes binding of libgeodock.so (argument marshalling only).
+
+Host inputs are numpy arrays; device outputs are torch CUDA tensors, whose
+data pointers and the current torch stream are handed to the C calls. PyTorch
+is used for device memory and streams only.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(HERE, "libgeodock.so")
+
+DOCK_OK = 0
+DOCK_ERR_INVALID_ARG = -1
+DOCK_ERR_TOPOLOGY = -2
+DOCK_ERR_OUT_OF_MEMORY = -3
+DOCK_ERR_CUDA = -4
+DOCK_ERR_TIMEOUT = -5
+DOCK_ERR_UNSUPPORTED = -6
+
+P = ctypes.POINTER
+
+
+class dock_pocket(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("h", ctypes.c_double),
+                ("origin", ctypes.c_double * 3), ("centre", ctypes.c_double * 3), ("K", P(ctypes.c_uint16)),
+                ("pts", P(ctypes.c_int32)), ("npts", ctypes.c_int)]
+
+
+class dock_ligand_batch(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("atom_off", P(ctypes.c_int32)), ("xyz", P(ctypes.c_float)),
+                ("bond_off", P(ctypes.c_int32)), ("bonds", P(ctypes.c_int32)), ("rot_off", P(ctypes.c_int32)),
+                ("rot", P(ctypes.c_int32)), ("id_base", ctypes.c_int64), ("ids", P(ctypes.c_int64))]
+
+
+class dock_knobs(ctypes.Structure):
+    _fields_ = [("hp_step", ctypes.c_double), ("lp_step", ctypes.c_double), ("threshold", ctypes.c_double),
+                ("repetitions", ctypes.c_int), ("n_poses", ctypes.c_int), ("enable_refinement", ctypes.c_int),
+                ("clip_box", ctypes.c_int), ("bump_thr", ctypes.c_double), ("score_mode", ctypes.c_int),
+                ("refine_steps", ctypes.c_int), ("seed", ctypes.c_uint64), ("plain_mode", ctypes.c_int)]
+
+
+class dock_result(ctypes.Structure):
+    _fields_ = [("score", ctypes.c_float), ("pose", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+RESULT_DTYPE = np.dtype([("score", np.float32), ("pose", np.int32), ("status", np.int32), ("reserved", np.int32)])
+
+
+class dock_trace(ctypes.Structure):
+    _fields_ = [("pmax", ctypes.c_int32), ("sweep_base", ctypes.c_void_p), ("chosen_k", ctypes.c_void_p),
+                ("cand_S", ctypes.c_void_p), ("cand_status", ctypes.c_void_p), ("pose_S", ctypes.c_void_p),
+                ("pose_init_S", ctypes.c_void_p), ("pose_status", ctypes.c_void_p), ("init_xyz", ctypes.c_void_p),
+                ("pose_xyz", ctypes.c_void_p)]
+
+
+class dock_tile(ctypes.Structure):
+    _fields_ = [("lanes_per_pose", ctypes.c_int), ("angles_per_chunk", ctypes.c_int), ("warps_per_cta", ctypes.c_int)]
+
+
+class dock_stats(ctypes.Structure):
+    _fields_ = [("candidates", ctypes.c_uint64), ("atom_updates", ctypes.c_uint64), ("pair_bounds", ctypes.c_uint64),
+                ("bump_pairs", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64), ("sweep_ms", ctypes.c_double)]
+
+
+def _load():
+    if not os.path.exists(library_path):
+        raise ImportError(f"{library_path} is missing: build it with `python -m paper_1901_06363_gb300.build` "
+                          "(there is no CPU fallback)")
+    L = ctypes.CDLL(library_path)
+    vp, i32p = ctypes.c_void_p, P(ctypes.c_int)
+    sig = {
+        "dock_create": ([P(vp), ctypes.c_int], ctypes.c_int),
+        "dock_destroy": ([vp], None),
+        "dock_last_error": ([vp], ctypes.c_char_p),
+        "dock_init_pocket": ([vp, P(dock_pocket), i32p], ctypes.c_int),
+        "dock_pocket_field": ([vp, ctypes.c_int, P(ctypes.c_uint16)], ctypes.c_int),
+        "dock_upload_ligands": ([vp, P(dock_ligand_batch), i32p], ctypes.c_int),
+        "dock_release_batch": ([vp, ctypes.c_int], ctypes.c_int),
+        "dock_run": ([vp, ctypes.c_int, P(ctypes.c_int32), ctypes.c_int, P(dock_knobs), vp, vp, ctypes.c_int, vp],
+                     ctypes.c_int),
+        "dock_run_trace": ([vp, ctypes.c_int, ctypes.c_int, P(dock_knobs), P(dock_trace), vp, vp], ctypes.c_int),
+        "dock_trace_pmax": ([P(dock_knobs)], ctypes.c_int),
+        "dock_set_tile": ([vp, P(dock_tile)], ctypes.c_int),
+        "dock_get_tile": ([vp, P(dock_tile)], ctypes.c_int),
+        "dock_autotune": ([vp, ctypes.c_int, ctypes.c_int, P(dock_knobs), P(dock_tile), vp], ctypes.c_int),
+        "dock_last_stats": ([vp, P(dock_stats)], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    return L
+
+
+lib = _load()
+
+
+class DockError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+def knobs_struct(kn) -> dock_knobs:
+    """dock_knobs from a knob dict (keys as in synth.configs.knobs)."""
+    k = dock_knobs()
+    k.hp_step = float(kn["hp_step"])
+    k.lp_step = float(kn.get("lp_step", kn["hp_step"]))
+    k.threshold = float(kn.get("threshold", 0.0))
+    k.repetitions = int(kn.get("repetitions", 1))
+    k.n_poses = int(kn.get("n_poses", 1))
+    k.enable_refinement = int(kn.get("enable_refinement", 0))
+    k.clip_box = int(kn.get("clip_box", 1))
+    k.bump_thr = float(kn.get("bump_thr", 2.0))
+    k.score_mode = int(kn.get("score_mode", 0))
+    k.refine_steps = 0
+    k.seed = int(kn.get("seed", 0))
+    k.plain_mode = int(kn.get("plain_mode", 0))
+    return k
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(P(t))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Docker:
+    """One dock_ctx on a CUDA device; methods mirror the C calls."""
+
+    def __init__(self, device: int = 0):
+        self._c = ctypes.c_void_p()
+        rc = lib.dock_create(ctypes.byref(self._c), device)
+        if rc != DOCK_OK:
+            raise DockError(rc, f"dock_create(device={device}) failed")
+        self._keep = []
+
+    def close(self):
+        if self._c:
+            lib.dock_destroy(self._c)
+            self._c = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != DOCK_OK:
+            raise DockError(rc, f"{what}: {lib.dock_last_error(self._c).decode()}")
+
+    # ---------------------------------------------------------------- inputs
+    def init_pocket(self, pk, K=None) -> int:
+        """dock_init_pocket: pk has dims, h, origin, centre, pts (voxel indices)."""
+        p = dock_pocket()
+        p.nx, p.ny, p.nz = (int(d) for d in pk.dims)
+        p.h = float(pk.h)
+        p.origin[:] = [float(v) for v in pk.origin]
+        p.centre[:] = [float(v) for v in pk.centre]
+        pts = np.ascontiguousarray(pk.pts, np.int32).reshape(-1, 3)
+        p.pts = _ptr(pts, ctypes.c_int32)
+        p.npts = len(pts)
+        if K is not None:
+            K = np.ascontiguousarray(K, np.uint16)
+            p.K = _ptr(K, ctypes.c_uint16)
+        pid = ctypes.c_int(-1)
+        self._check(lib.dock_init_pocket(self._c, ctypes.byref(p), ctypes.byref(pid)), "dock_init_pocket")
+        return pid.value
+
+    def pocket_field(self, pid: int, dims) -> np.ndarray:
+        nx, ny, nz = dims
+        K = np.zeros(nx * ny * nz, np.uint16)
+        self._check(lib.dock_pocket_field(self._c, pid, _ptr(K, ctypes.c_uint16)), "dock_pocket_field")
+        return K.reshape(nz, ny, nx)
+
+    def upload_ligands(self, batch, ids=None) -> int:
+        b = dock_ligand_batch()
+        b.n = batch.n
+        arrs = [np.ascontiguousarray(batch.atom_off, np.int32), np.ascontiguousarray(batch.xyz, np.float32),
+                np.ascontiguousarray(batch.bond_off, np.int32), np.ascontiguousarray(batch.bonds, np.int32),
+                np.ascontiguousarray(batch.rot_off, np.int32), np.ascontiguousarray(batch.rot, np.int32)]
+        b.atom_off = _ptr(arrs[0], ctypes.c_int32)
+        b.xyz = _ptr(arrs[1], ctypes.c_float)
+        b.bond_off = _ptr(arrs[2], ctypes.c_int32)
+        b.bonds = _ptr(arrs[3], ctypes.c_int32)
+        b.rot_off = _ptr(arrs[4], ctypes.c_int32)
+        b.rot = _ptr(arrs[5], ctypes.c_int32)
+        b.id_base = int(batch.id_base)
+        if ids is not None:
+            ids = np.ascontiguousarray(ids, np.int64)
+            b.ids = _ptr(ids, ctypes.c_int64)
+        bid = ctypes.c_int(-1)
+        self._check(lib.dock_upload_ligands(self._c, ctypes.byref(b), ctypes.byref(bid)), "dock_upload_ligands")
+        return bid.value
+
+    def release_batch(self, bid: int):
+        self._check(lib.dock_release_batch(self._c, bid), "dock_release_batch")
+
+    # ------------------------------------------------------------------- runs
+    def run(self, bid: int, pocket_ids, kn, n: int, natoms: int, xyz: bool = True, out=None, xyz_out=None,
+            stream=None):
+        """dock_run with host outputs (numpy) unless `out` is a torch CUDA tensor.
+
+        Returns (results structured array or tensor, xyz array or tensor or None)."""
+        pids = np.ascontiguousarray(pocket_ids, np.int32).reshape(-1)
+        k = knobs_struct(kn)
+        npk = len(pids)
+        on_dev = out is not None and hasattr(out, "data_ptr")
+        if on_dev:
+            res_ptr = ctypes.c_void_p(out.data_ptr())
+            xyz_ptr = ctypes.c_void_p(xyz_out.data_ptr()) if xyz_out is not None else None
+            st = _stream_ptr(stream)
+        else:
+            out = np.zeros(npk * n, RESULT_DTYPE)
+            res_ptr = ctypes.c_void_p(out.ctypes.data)
+            if xyz:
+                xyz_out = np.zeros((npk, natoms, 3), np.float32)
+                xyz_ptr = ctypes.c_void_p(xyz_out.ctypes.data)
+            else:
+                xyz_out, xyz_ptr = None, None
+            st = _stream_ptr(stream) if stream is not None else None
+        rc = lib.dock_run(self._c, bid, _ptr(pids, ctypes.c_int32), npk, ctypes.byref(k), res_ptr, xyz_ptr,
+                          1 if on_dev else 0, st)
+        self._check(rc, "dock_run")
+        return out, xyz_out
+
+    def run_trace(self, bid: int, pid: int, kn, batch):
+        """dock_run_trace: per-candidate trace (device buffers via torch), returned as numpy arrays."""
+        import torch
+        k = knobs_struct(kn)
+        pmax = lib.dock_trace_pmax(ctypes.byref(k))
+        N = int(kn["n_poses"])
+        _, t = batch.sizes()
+        nsw = int(kn["repetitions"]) * 2 * t.astype(np.int64)
+        total = int((nsw * N).sum())
+        natoms = int(batch.atom_off[-1])
+        dev = torch.device("cuda")
+        bufs = dict(chosen_k=torch.zeros(max(total, 1), dtype=torch.int32, device=dev),
+                    cand_S=torch.zeros(max(total * pmax, 1), dtype=torch.float32, device=dev),
+                    cand_status=torch.zeros(max(total * pmax, 1), dtype=torch.int32, device=dev),
+                    pose_S=torch.zeros(max(batch.n * N, 1), dtype=torch.float32, device=dev),
+                    pose_init_S=torch.zeros(max(batch.n * N, 1), dtype=torch.float32, device=dev),
+                    pose_status=torch.zeros(max(batch.n * N, 1), dtype=torch.int32, device=dev),
+                    init_xyz=torch.zeros(max(natoms * N * 3, 1), dtype=torch.float32, device=dev),
+                    pose_xyz=torch.zeros(max(natoms * N * 3, 1), dtype=torch.float32, device=dev))
+        tr = dock_trace()
+        tr.pmax = pmax
+        for name, tns in bufs.items():
+            setattr(tr, name, tns.data_ptr())
+        out = np.zeros(batch.n, RESULT_DTYPE)
+        torch.cuda.synchronize()
+        rc = lib.dock_run_trace(self._c, bid, pid, ctypes.byref(k), ctypes.byref(tr), ctypes.c_void_p(out.ctypes.data),
+                                _stream_ptr(None))
+        self._check(rc, "dock_run_trace")
+        res = {name: tns.cpu().numpy()[:{"chosen_k": total, "cand_S": total * pmax, "cand_status": total * pmax,
+                                          "pose_S": batch.n * N, "pose_init_S": batch.n * N,
+                                          "pose_status": batch.n * N, "init_xyz": natoms * N * 3,
+                                          "pose_xyz": natoms * N * 3}[name]] for name, tns in bufs.items()}
+        res["pmax"] = pmax
+        res["result"] = out
+        return res
+
+    # ------------------------------------------------------------------ tiles
+    def set_tile(self, lanes_per_pose=0, angles_per_chunk=0, warps_per_cta=0):
+        t = dock_tile(lanes_per_pose, angles_per_chunk, warps_per_cta)
+        self._check(lib.dock_set_tile(self._c, ctypes.byref(t)), "dock_set_tile")
+
+    def autotune(self, bid: int, pid: int, kn, stream=None):
+        k = knobs_struct(kn)
+        t = dock_tile()
+        self._check(lib.dock_autotune(self._c, bid, pid, ctypes.byref(k), ctypes.byref(t), _stream_ptr(stream)),
+                    "dock_autotune")
+        return (t.lanes_per_pose, t.angles_per_chunk, t.warps_per_cta)
+
+    def stats(self):
+        s = dock_stats()
+        self._check(lib.dock_last_stats(self._c, ctypes.byref(s)), "dock_last_stats")
+        return {name: getattr(s, name) for name, _ in dock_stats._fields_}

@@ -1,0 +1,884 @@
+// Host side of the C ABI declared in include/geodock.h: context and device
+// memory, topology checks and fragment tables (Alg. 1 "get the list of
+// rotamers", "grow the right and left fragment"), run planning (work order,
+// angle tables), the persistent batched launch in a CUDA graph, the plain
+// one-launch-per-pair form, and the trace run.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/geodock.h"
+#define GD_DEFINE_AUX_KERNELS
+#include "geodock_kernels.cuh"
+#include "geodock_launch.h"
+
+using namespace gd;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+    cudaError_t ensure(size_t bytes) {
+        if (bytes <= n && p) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+        cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
+        if (e == cudaSuccess) n = std::max<size_t>(bytes, 16);
+        return e;
+    }
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+struct PocketH {
+    bool live = false;
+    PocketDev d{};
+    std::unique_ptr<DevBuf> K;
+};
+
+struct BatchH {
+    bool live = false;
+    int n = 0, natoms = 0, lmax = 1, nside_total = 0;
+    std::vector<int> l, nside;            // per ligand
+    std::vector<int> side_m, side_nmov, side_nfixB;  // per side
+    std::vector<int> side_off;
+    std::vector<int> atom_off;
+    std::unique_ptr<DevBuf> lig, side, idx, xyz0;
+};
+
+// Everything a batched run needs that depends on (batch, pockets, knobs, tile).
+struct Plan {
+    int ntask = 0, npairs = 0;
+    std::unique_ptr<DevBuf> tasks, pockets, cs_hp, cs_lp, cs_peel;
+    SweepParams P{};
+    FinalParams F{};
+    int kc = 12, Q = 1, W = 4, grid = 1, block = 128;
+    size_t smem = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t exec_stream = nullptr;
+    ~Plan() {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
+
+}  // namespace
+
+struct dock_ctx {
+    int device = 0;
+    int num_sms = 1;
+    std::string err;
+    std::vector<PocketH> pockets;
+    std::vector<BatchH> batches;
+    dock_tile tile{0, 0, 0};           // forced shape (0 = automatic)
+    std::map<std::string, dock_tile> tuned;  // autotuned shapes per (batch, knobs)
+    DevBuf counter, pose_key, pose_xyz, res, xyz_res;
+    std::map<std::string, std::unique_ptr<Plan>> plans;
+    dock_stats stats{};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the sweep kernel(s) of the last run
+    bool timed = false;
+    ~dock_ctx() {
+        plans.clear();
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+    }
+};
+
+namespace {
+
+int fail(dock_ctx* c, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+#define CK(call)                                                                                           \
+    do {                                                                                                   \
+        cudaError_t e_ = (call);                                                                           \
+        if (e_ != cudaSuccess)                                                                             \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? DOCK_ERR_OUT_OF_MEMORY : DOCK_ERR_CUDA,     \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);              \
+    } while (0)
+
+int n_angles(double step) {
+    int P = (int)std::ceil(360.0 / step);
+    while (P > 1 && (P - 1) * step >= 360.0) --P;
+    while (P * step < 360.0) ++P;
+    return P;
+}
+
+// Tile of tile peeling (Eq. 3 reading): the divisor of 360 that is a multiple
+// of the step and lies nearest to sqrt(360 step); ties to the smaller one.
+int peel_tile(double step) {
+    double target = std::sqrt(360.0 * step);
+    int best = -1;
+    double bestd = 1e300;
+    for (int x = 1; x <= 360; ++x) {
+        if (360 % x) continue;
+        double q = x / step;
+        if (std::fabs(q - std::round(q)) > 1e-9 || q < 1.0 - 1e-9) continue;
+        double d = std::fabs(x - target);
+        if (d < bestd - 1e-12) {
+            bestd = d;
+            best = x;
+        }
+    }
+    return best;
+}
+
+std::vector<float2> angle_table(const std::vector<double>& deg) {
+    std::vector<float2> t(deg.size());
+    const double rad = 3.14159265358979323846 / 180.0;
+    for (size_t i = 0; i < deg.size(); ++i) t[i] = make_float2((float)std::cos(deg[i] * rad), (float)std::sin(deg[i] * rad));
+    return t;
+}
+
+int check_knobs(dock_ctx* ctx, const dock_knobs* k) {
+    if (!k) return fail(ctx, DOCK_ERR_INVALID_ARG, "knobs: NULL");
+    if (!(k->hp_step >= 1.0 && k->hp_step <= 360.0) || !(k->lp_step >= 1.0 && k->lp_step <= 360.0))
+        return fail(ctx, DOCK_ERR_INVALID_ARG, "knobs: steps must lie in [1, 360] degrees");
+    if (k->repetitions < 0 || k->repetitions > 1000) return fail(ctx, DOCK_ERR_INVALID_ARG, "knobs: repetitions");
+    if (k->n_poses < 1 || k->n_poses > DOCK_MAX_POSES) return fail(ctx, DOCK_ERR_INVALID_ARG, "knobs: n_poses");
+    if (!(k->bump_thr >= 0.0) || !std::isfinite(k->bump_thr)) return fail(ctx, DOCK_ERR_INVALID_ARG, "knobs: bump_thr");
+    if (!std::isfinite(k->threshold)) return fail(ctx, DOCK_ERR_INVALID_ARG, "knobs: threshold");
+    if (k->score_mode != 0 && k->score_mode != 1) return fail(ctx, DOCK_ERR_INVALID_ARG, "knobs: score_mode");
+    if (k->refine_steps != 0) return fail(ctx, DOCK_ERR_UNSUPPORTED, "knobs: refinement runs through dock_refine");
+    if (k->enable_refinement && peel_tile(k->hp_step) < 0)
+        return fail(ctx, DOCK_ERR_UNSUPPORTED, "knobs: no tile size divides 360 for this step");
+    return DOCK_OK;
+}
+
+int trace_pmax(const dock_knobs* k) {
+    int p = std::max(n_angles(k->hp_step), n_angles(k->lp_step));
+    if (k->enable_refinement) {
+        int x = peel_tile(k->hp_step);
+        p = std::max(p, 1 + 360 / x + (int)std::lround(x / k->hp_step));
+    }
+    return p;
+}
+
+// Default tile shape: lanes per pose so that a warp holds no more poses than
+// the run has, and angles per chunk to cover a hp sweep in few chunks.
+dock_tile default_tile(const dock_knobs* k) {
+    dock_tile t;
+    int N = k->n_poses;
+    t.lanes_per_pose = N >= 32 ? 1 : (N >= 16 ? 2 : (N >= 8 ? 4 : 8));
+    int per_lane = (n_angles(k->hp_step) - 1 + t.lanes_per_pose - 1) / t.lanes_per_pose;
+    t.angles_per_chunk = per_lane <= 8 ? 8 : (per_lane <= 12 ? 12 : (per_lane <= 18 ? 18 : 36));
+    t.warps_per_cta = 4;
+    return t;
+}
+
+cudaError_t launch_sweep(int kc, const SweepParams& P, int mode, int clip, int grid, int block, size_t smem,
+                         cudaStream_t s) {
+    switch (kc) {
+        case 8: return launch_sweep_kc8(P, mode, clip, grid, block, smem, s);
+        case 12: return launch_sweep_kc12(P, mode, clip, grid, block, smem, s);
+        case 18: return launch_sweep_kc18(P, mode, clip, grid, block, smem, s);
+        default: return launch_sweep_kc36(P, mode, clip, grid, block, smem, s);
+    }
+}
+cudaError_t occupancy(int kc, int mode, int clip, int block, size_t smem, int* n) {
+    switch (kc) {
+        case 8: return occupancy_kc8(mode, clip, block, smem, n);
+        case 12: return occupancy_kc12(mode, clip, block, smem, n);
+        case 18: return occupancy_kc18(mode, clip, block, smem, n);
+        default: return occupancy_kc36(mode, clip, block, smem, n);
+    }
+}
+
+std::string plan_key(int batch_id, const int32_t* pids, int np, const dock_knobs* k, const dock_tile& t, int plain) {
+    char buf[512];
+    snprintf(buf, sizeof buf, "%d|%a|%a|%a|%d|%d|%d|%d|%a|%d|%llu|%d|%d|%d|%d|", batch_id, k->hp_step, k->lp_step,
+             k->threshold, k->repetitions, k->n_poses, k->enable_refinement, k->clip_box, k->bump_thr, k->score_mode,
+             (unsigned long long)k->seed, t.lanes_per_pose, t.angles_per_chunk, t.warps_per_cta, plain);
+    std::string s = buf;
+    for (int i = 0; i < np; ++i) s += std::to_string(pids[i]) + ",";
+    return s;
+}
+
+// Estimated cost of one warp task (pose group) of ligand b: candidate
+// evaluations times moving atoms, plus the bump partner scans per chunk.
+double task_cost(const BatchH& B, int b, const dock_knobs* k, int Q, int kc) {
+    int P_hp = n_angles(k->hp_step), P_lp = n_angles(k->lp_step);
+    double c = 0;
+    for (int s = 0; s < B.nside[b]; ++s) {
+        int si = B.side_off[b] + s;
+        bool coarse = (double)B.side_m[si] / (double)B.l[b] <= k->threshold;
+        int ncand = coarse ? P_lp - 1 : P_hp - 1;
+        if (k->enable_refinement && !coarse) {
+            int x = peel_tile(k->hp_step);
+            ncand = 360 / x + (int)std::lround(x / k->hp_step);
+        }
+        int per_lane = (ncand + Q - 1) / Q;
+        int chunks = (per_lane + kc - 1) / kc;
+        c += (double)B.side_nmov[si] * (chunks * kc * 1.0 + chunks * B.side_nfixB[si] * 0.6) + B.l[b];
+    }
+    return c * std::max(k->repetitions, 1) + B.l[b] * 4.0;
+}
+
+}  // namespace
+
+// ======================================================================== API
+
+extern "C" {
+
+int dock_create(dock_ctx** out, int device) {
+    if (!out) return DOCK_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return DOCK_ERR_CUDA;
+    if (cudaSetDevice(device) != cudaSuccess) return DOCK_ERR_CUDA;
+    dock_ctx* c = new dock_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+        delete c;
+        return DOCK_ERR_CUDA;
+    }
+    *out = c;
+    return DOCK_OK;
+}
+
+void dock_destroy(dock_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    delete ctx;
+}
+
+const char* dock_last_error(const dock_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int dock_init_pocket(dock_ctx* ctx, const dock_pocket* p, int* pocket_id) {
+    if (!ctx || !p || !pocket_id) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_init_pocket: NULL argument");
+    CK(cudaSetDevice(ctx->device));
+    if (p->nx < 2 || p->ny < 2 || p->nz < 2 || p->nx > DOCK_MAX_GRID || p->ny > DOCK_MAX_GRID || p->nz > DOCK_MAX_GRID)
+        return fail(ctx, DOCK_ERR_INVALID_ARG, "pocket: grid size out of range");
+    if (!(p->h > 0.0) || !std::isfinite(p->h)) return fail(ctx, DOCK_ERR_INVALID_ARG, "pocket: h must be > 0");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(p->origin[a]) || !std::isfinite(p->centre[a]))
+            return fail(ctx, DOCK_ERR_INVALID_ARG, "pocket: non-finite origin/centre");
+    int64_t nv = (int64_t)p->nx * p->ny * p->nz;
+    // the largest squared distance between voxels must fit the 16-bit field
+    int64_t dmax = (int64_t)(p->nx - 1) * (p->nx - 1) + (int64_t)(p->ny - 1) * (p->ny - 1) + (int64_t)(p->nz - 1) * (p->nz - 1);
+    PocketH ph;
+    ph.K.reset(new DevBuf());
+    CK(ph.K->ensure(nv * sizeof(uint16_t)));
+    if (p->K) {
+        for (int64_t v = 0; v < nv; ++v)
+            if (p->K[v] < 1) return fail(ctx, DOCK_ERR_INVALID_ARG, "pocket: field values must be >= 1");
+        CK(cudaMemcpy(ph.K->p, p->K, nv * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    } else {
+        if (!p->pts || p->npts < 1) return fail(ctx, DOCK_ERR_INVALID_ARG, "pocket: no probe points");
+        if (dmax > 65535) return fail(ctx, DOCK_ERR_INVALID_ARG, "pocket: grid too large for 16-bit distances");
+        std::vector<int4> pts(p->npts);
+        for (int j = 0; j < p->npts; ++j) {
+            int x = p->pts[3 * j], y = p->pts[3 * j + 1], z = p->pts[3 * j + 2];
+            if (x < 0 || y < 0 || z < 0 || x >= p->nx || y >= p->ny || z >= p->nz)
+                return fail(ctx, DOCK_ERR_INVALID_ARG, "pocket: probe point %d outside the grid", j);
+            pts[j] = make_int4(x, y, z, 0);
+        }
+        DevBuf dp;
+        CK(dp.ensure(pts.size() * sizeof(int4)));
+        CK(cudaMemcpy(dp.p, pts.data(), pts.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        int threads = 256;
+        int64_t blocks = (nv + threads - 1) / threads;
+        field_kernel<<<(unsigned)blocks, threads>>>(ph.K->as<uint16_t>(), p->nx, p->ny, p->nz, dp.as<int4>(), p->npts);
+        CK(cudaGetLastError());
+        CK(cudaDeviceSynchronize());
+    }
+    ph.d.K = ph.K->as<uint16_t>();
+    ph.d.nx = p->nx;
+    ph.d.ny = p->ny;
+    ph.d.nz = p->nz;
+    ph.d.h = p->h;
+    for (int a = 0; a < 3; ++a) {
+        ph.d.origin[a] = p->origin[a];
+        ph.d.centre[a] = p->centre[a];
+    }
+    ph.live = true;
+    ctx->pockets.push_back(std::move(ph));
+    *pocket_id = (int)ctx->pockets.size() - 1;
+    return DOCK_OK;
+}
+
+int dock_pocket_field(dock_ctx* ctx, int pocket_id, uint16_t* K) {
+    if (!ctx || !K || pocket_id < 0 || pocket_id >= (int)ctx->pockets.size() || !ctx->pockets[pocket_id].live)
+        return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_pocket_field: bad arguments");
+    CK(cudaSetDevice(ctx->device));
+    const PocketDev& d = ctx->pockets[pocket_id].d;
+    CK(cudaMemcpy(K, d.K, (size_t)d.nx * d.ny * d.nz * sizeof(uint16_t), cudaMemcpyDeviceToHost));
+    return DOCK_OK;
+}
+
+int dock_upload_ligands(dock_ctx* ctx, const dock_ligand_batch* b, int* batch_id) {
+    if (!ctx || !b || !batch_id) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_upload_ligands: NULL argument");
+    if (b->n < 0) return fail(ctx, DOCK_ERR_INVALID_ARG, "batch: n < 0");
+    if (b->n > 0 && (!b->atom_off || !b->xyz || !b->bond_off || !b->rot_off))
+        return fail(ctx, DOCK_ERR_INVALID_ARG, "batch: NULL array");
+    CK(cudaSetDevice(ctx->device));
+    BatchH B;
+    B.n = b->n;
+    std::vector<LigDev> lig(b->n);
+    std::vector<SideDev> sides;
+    std::vector<uint8_t> idx;
+    if (b->n > 0 && (b->atom_off[0] != 0 || b->bond_off[0] != 0 || b->rot_off[0] != 0))
+        return fail(ctx, DOCK_ERR_INVALID_ARG, "batch: offsets must start at 0");
+    for (int i = 0; i < b->n; ++i) {
+        int a0 = b->atom_off[i], l = b->atom_off[i + 1] - a0;
+        int e0 = b->bond_off[i], ne = b->bond_off[i + 1] - e0;
+        int r0 = b->rot_off[i], nr = b->rot_off[i + 1] - r0;
+        if (l < 1 || l > DOCK_MAX_ATOMS) return fail(ctx, DOCK_ERR_INVALID_ARG, "ligand %d: %d atoms", i, l);
+        if (ne < 0 || nr < 0 || (ne > 0 && !b->bonds) || (nr > 0 && !b->rot))
+            return fail(ctx, DOCK_ERR_INVALID_ARG, "ligand %d: bad bond/rotamer offsets", i);
+        std::vector<std::vector<int>> adj(l);
+        for (int e = 0; e < ne; ++e) {
+            int u = b->bonds[2 * (e0 + e)], v = b->bonds[2 * (e0 + e) + 1];
+            if (u < 0 || v < 0 || u >= l || v >= l || u == v)
+                return fail(ctx, DOCK_ERR_INVALID_ARG, "ligand %d: bond %d has bad atoms", i, e);
+            adj[u].push_back(v);
+            adj[v].push_back(u);
+        }
+        double g[3] = {0, 0, 0};
+        for (int a = 0; a < l; ++a)
+            for (int d = 0; d < 3; ++d) {
+                float x = b->xyz[3 * (a0 + a) + d];
+                if (!std::isfinite(x) || std::fabs(x) > 1e5f)
+                    return fail(ctx, DOCK_ERR_INVALID_ARG, "ligand %d: coordinate out of range", i);
+                g[d] += (double)x;
+            }
+        LigDev& L = lig[i];
+        L.atom_off = a0;
+        L.l = l;
+        L.nside = 2 * nr;
+        L.side_off = (int)sides.size();
+        for (int d = 0; d < 3; ++d) L.g[d] = g[d] / l;
+        L.id = b->ids ? b->ids[i] : b->id_base + i;
+        B.l.push_back(l);
+        B.nside.push_back(2 * nr);
+        B.side_off.push_back((int)sides.size());
+        B.atom_off.push_back(a0);
+        B.lmax = std::max(B.lmax, l);
+        for (int r = 0; r < nr; ++r) {
+            int e = b->rot[r0 + r];
+            if (e < 0 || e >= ne) return fail(ctx, DOCK_ERR_INVALID_ARG, "ligand %d: rotatable bond index %d", i, e);
+            int u = b->bonds[2 * (e0 + e)], v = b->bonds[2 * (e0 + e) + 1];
+            if (u > v) std::swap(u, v);
+            // left fragment: atoms reachable from u without crossing (u, v)
+            std::vector<char> left(l, 0);
+            std::vector<int> st{u};
+            left[u] = 1;
+            while (!st.empty()) {
+                int x = st.back();
+                st.pop_back();
+                for (int y : adj[x]) {
+                    if ((x == u && y == v) || (x == v && y == u)) continue;
+                    if (!left[y]) {
+                        left[y] = 1;
+                        st.push_back(y);
+                    }
+                }
+            }
+            if (left[v]) return fail(ctx, DOCK_ERR_TOPOLOGY, "ligand %d: rotatable bond %d lies on a ring", i, e);
+            for (int side = 0; side < 2; ++side) {
+                // side 0: the left fragment moves (c = u, b = v); side 1: the right one (c = v, b = u)
+                int c = side == 0 ? u : v, bb = side == 0 ? v : u;
+                SideDev sd{};
+                sd.c = (uint8_t)c;
+                sd.b = (uint8_t)bb;
+                sd.mov_off = (int)idx.size();
+                int m = 0;
+                for (int a = 0; a < l; ++a) {
+                    bool moving = side == 0 ? left[a] != 0 : left[a] == 0;
+                    if (!moving) continue;
+                    ++m;
+                    if (a != c) idx.push_back((uint8_t)a);
+                }
+                sd.m = (uint8_t)m;
+                sd.nmov = (uint8_t)(m - 1);
+                sd.fix_off = (int)idx.size();
+                for (int a = 0; a < l; ++a) {
+                    bool moving = side == 0 ? left[a] != 0 : left[a] == 0;
+                    if (!moving && a != bb) idx.push_back((uint8_t)a);
+                }
+                idx.push_back((uint8_t)bb);
+                idx.push_back((uint8_t)c);
+                sd.nfixB = (uint8_t)(l - m - 1);
+                sd.nfixS = (uint8_t)(l - m + 1);
+                sides.push_back(sd);
+                B.side_m.push_back(m);
+                B.side_nmov.push_back(m - 1);
+                B.side_nfixB.push_back(l - m - 1);
+            }
+        }
+    }
+    B.natoms = b->n > 0 ? b->atom_off[b->n] : 0;
+    B.nside_total = (int)sides.size();
+    B.lig.reset(new DevBuf());
+    B.side.reset(new DevBuf());
+    B.idx.reset(new DevBuf());
+    B.xyz0.reset(new DevBuf());
+    CK(B.lig->ensure(lig.size() * sizeof(LigDev)));
+    CK(B.side->ensure(sides.size() * sizeof(SideDev)));
+    CK(B.idx->ensure(idx.size()));
+    CK(B.xyz0->ensure((size_t)B.natoms * 3 * sizeof(float)));
+    if (!lig.empty()) CK(cudaMemcpy(B.lig->p, lig.data(), lig.size() * sizeof(LigDev), cudaMemcpyHostToDevice));
+    if (!sides.empty()) CK(cudaMemcpy(B.side->p, sides.data(), sides.size() * sizeof(SideDev), cudaMemcpyHostToDevice));
+    if (!idx.empty()) CK(cudaMemcpy(B.idx->p, idx.data(), idx.size(), cudaMemcpyHostToDevice));
+    if (B.natoms) CK(cudaMemcpy(B.xyz0->p, b->xyz, (size_t)B.natoms * 3 * sizeof(float), cudaMemcpyHostToDevice));
+    B.live = true;
+    ctx->batches.push_back(std::move(B));
+    *batch_id = (int)ctx->batches.size() - 1;
+    return DOCK_OK;
+}
+
+int dock_release_batch(dock_ctx* ctx, int batch_id) {
+    if (!ctx || batch_id < 0 || batch_id >= (int)ctx->batches.size() || !ctx->batches[batch_id].live)
+        return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_release_batch: bad batch");
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaDeviceSynchronize());
+    ctx->batches[batch_id] = BatchH();
+    std::string pre = std::to_string(batch_id) + "|";
+    for (auto it = ctx->plans.begin(); it != ctx->plans.end();)
+        it = it->first.compare(0, pre.size(), pre) == 0 ? ctx->plans.erase(it) : std::next(it);
+    return DOCK_OK;
+}
+
+int dock_trace_pmax(const dock_knobs* k) { return k ? trace_pmax(k) : -1; }
+
+int dock_set_tile(dock_ctx* ctx, const dock_tile* t) {
+    if (!ctx || !t) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_set_tile: NULL");
+    if (t->lanes_per_pose && t->lanes_per_pose != 1 && t->lanes_per_pose != 2 && t->lanes_per_pose != 4 &&
+        t->lanes_per_pose != 8)
+        return fail(ctx, DOCK_ERR_INVALID_ARG, "tile: lanes_per_pose must be 1, 2, 4 or 8");
+    if (t->angles_per_chunk && t->angles_per_chunk != 8 && t->angles_per_chunk != 12 && t->angles_per_chunk != 18 &&
+        t->angles_per_chunk != 36)
+        return fail(ctx, DOCK_ERR_INVALID_ARG, "tile: angles_per_chunk must be 8, 12, 18 or 36");
+    if (t->warps_per_cta < 0 || t->warps_per_cta > 8) return fail(ctx, DOCK_ERR_INVALID_ARG, "tile: warps 1..8");
+    ctx->tile = *t;
+    return DOCK_OK;
+}
+
+int dock_get_tile(const dock_ctx* ctx, dock_tile* t) {
+    if (!ctx || !t) return DOCK_ERR_INVALID_ARG;
+    *t = ctx->tile;
+    return DOCK_OK;
+}
+
+int dock_last_stats(const dock_ctx* ctx_, dock_stats* s) {
+    if (!ctx_ || !s) return DOCK_ERR_INVALID_ARG;
+    dock_ctx* ctx = const_cast<dock_ctx*>(ctx_);
+    if (ctx->timed) {
+        float ms = 0.f;
+        CK(cudaEventSynchronize(ctx->ev1));
+        CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+        ctx->stats.sweep_ms = ms;
+        ctx->timed = false;
+    }
+    *s = ctx->stats;
+    return DOCK_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Resolve the tile shape: forced fields, else the autotuned shape for this
+// (batch, knobs), else the default.
+dock_tile resolve_tile(dock_ctx* ctx, int batch_id, const dock_knobs* k) {
+    dock_tile t = default_tile(k);
+    auto it = ctx->tuned.find(plan_key(batch_id, nullptr, 0, k, dock_tile{0, 0, 0}, 0));
+    if (it != ctx->tuned.end()) t = it->second;
+    if (ctx->tile.lanes_per_pose) t.lanes_per_pose = ctx->tile.lanes_per_pose;
+    if (ctx->tile.angles_per_chunk) t.angles_per_chunk = ctx->tile.angles_per_chunk;
+    if (ctx->tile.warps_per_cta) t.warps_per_cta = ctx->tile.warps_per_cta;
+    return t;
+}
+
+int upload(dock_ctx* ctx, std::unique_ptr<DevBuf>& buf, const void* src, size_t bytes) {
+    buf.reset(new DevBuf());
+    CK(buf->ensure(bytes));
+    if (bytes) CK(cudaMemcpy(buf->p, src, bytes, cudaMemcpyHostToDevice));
+    return DOCK_OK;
+}
+
+// Build (or fetch) the plan of a run: pockets, angle tables, tasks, launch shape.
+int get_plan(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const dock_knobs* k, int plain, Plan** out) {
+    const dock_tile t = resolve_tile(ctx, batch_id, k);
+    std::string key = plan_key(batch_id, pids, np, k, t, plain);
+    auto it = ctx->plans.find(key);
+    if (it != ctx->plans.end()) {
+        *out = it->second.get();
+        return DOCK_OK;
+    }
+    const BatchH& B = ctx->batches[batch_id];
+    std::unique_ptr<Plan> pl(new Plan());
+    pl->Q = t.lanes_per_pose;
+    pl->kc = t.angles_per_chunk;
+    pl->W = t.warps_per_cta;
+    pl->block = 32 * pl->W;
+    const int G = 32 / pl->Q;
+    const int N = k->n_poses;
+    const int ngroup = (N + G - 1) / G;
+    pl->npairs = np * B.n;
+    // pockets
+    std::vector<PocketDev> pd(np);
+    for (int i = 0; i < np; ++i) pd[i] = ctx->pockets[pids[i]].d;
+    int rc = upload(ctx, pl->pockets, pd.data(), pd.size() * sizeof(PocketDev));
+    if (rc) return rc;
+    // angle tables (host FP64 cos/sin rounded to FP32)
+    const int P_hp = n_angles(k->hp_step), P_lp = n_angles(k->lp_step);
+    std::vector<double> a_hp(P_hp), a_lp(P_lp), a_peel;
+    for (int i = 0; i < P_hp; ++i) a_hp[i] = i * k->hp_step;
+    for (int i = 0; i < P_lp; ++i) a_lp[i] = i * k->lp_step;
+    int n_tiles = 0, per_tile = 0;
+    if (k->enable_refinement) {
+        int x = peel_tile(k->hp_step);
+        n_tiles = 360 / x;
+        per_tile = (int)std::lround(x / k->hp_step);
+        for (int i = 0; i < n_tiles; ++i) a_peel.push_back(i * x + 0.5 * x);
+    } else {
+        a_peel.push_back(0.0);
+    }
+    if ((rc = upload(ctx, pl->cs_hp, angle_table(a_hp).data(), P_hp * sizeof(float2)))) return rc;
+    if ((rc = upload(ctx, pl->cs_lp, angle_table(a_lp).data(), P_lp * sizeof(float2)))) return rc;
+    if ((rc = upload(ctx, pl->cs_peel, angle_table(a_peel).data(), a_peel.size() * sizeof(float2)))) return rc;
+    // tasks: (pair, pose group); batched form in descending cost (longest first),
+    // plain form in pair order
+    std::vector<int2> tasks;
+    tasks.reserve((size_t)pl->npairs * ngroup);
+    std::vector<double> cost;
+    for (int pk = 0; pk < np; ++pk)
+        for (int b = 0; b < B.n; ++b) {
+            double c = task_cost(B, b, k, pl->Q, pl->kc);
+            for (int g = 0; g < ngroup; ++g) {
+                tasks.push_back(make_int2(pk * B.n + b, g));
+                cost.push_back(c);
+            }
+        }
+    if (!plain) {
+        std::vector<int> order(tasks.size());
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b2) { return cost[a] > cost[b2]; });
+        std::vector<int2> sorted(tasks.size());
+        for (size_t i = 0; i < order.size(); ++i) sorted[i] = tasks[order[i]];
+        tasks.swap(sorted);
+    }
+    pl->ntask = (int)tasks.size();
+    if ((rc = upload(ctx, pl->tasks, tasks.data(), tasks.size() * sizeof(int2)))) return rc;
+    // scratch, shared by every plan of the context: growing it moves the
+    // buffers, so every cached plan (and its captured graph) is dropped
+    {
+        const size_t need[5] = {sizeof(unsigned), (size_t)pl->npairs * N * sizeof(unsigned long long),
+                                (size_t)np * B.natoms * N * 3 * sizeof(float), (size_t)pl->npairs * sizeof(dock_result),
+                                (size_t)np * B.natoms * 3 * sizeof(float)};
+        DevBuf* bufs[5] = {&ctx->counter, &ctx->pose_key, &ctx->pose_xyz, &ctx->res, &ctx->xyz_res};
+        bool grow = false;
+        for (int i = 0; i < 5; ++i) grow = grow || !bufs[i]->p || bufs[i]->n < need[i];
+        if (grow) {
+            CK(cudaDeviceSynchronize());
+            ctx->plans.clear();
+            for (int i = 0; i < 5; ++i) CK(bufs[i]->ensure(need[i]));
+        }
+    }
+    SweepParams& P = pl->P;
+    P.lig = B.lig->as<LigDev>();
+    P.side = B.side->as<SideDev>();
+    P.idx = B.idx->as<uint8_t>();
+    P.xyz0 = B.xyz0->as<float>();
+    P.pockets = pl->pockets->as<PocketDev>();
+    P.tasks = pl->tasks->as<int2>();
+    P.ntask = pl->ntask;
+    P.nlig = B.n;
+    P.natoms = B.natoms;
+    P.counter = ctx->counter.as<unsigned>();
+    P.n_poses = N;
+    P.repetitions = k->repetitions;
+    P.Q = pl->Q;
+    P.lmax = B.lmax;
+    P.threshold = k->threshold;
+    P.bump_thr = k->bump_thr;
+    P.seed = k->seed;
+    P.cs_hp = pl->cs_hp->as<float2>();
+    P.cs_lp = pl->cs_lp->as<float2>();
+    P.P_hp = P_hp;
+    P.P_lp = P_lp;
+    P.peel = k->enable_refinement ? 1 : 0;
+    P.cs_peel = pl->cs_peel->as<float2>();
+    P.n_tiles = n_tiles;
+    P.per_tile = per_tile;
+    P.pose_key = ctx->pose_key.as<unsigned long long>();
+    P.pose_xyz = ctx->pose_xyz.as<float>();
+    P.trace_on = 0;
+    pl->smem = (size_t)pl->W * B.lmax * 3 * G * sizeof(float);
+    int per_sm = 0;
+    CK(occupancy(pl->kc, k->score_mode, k->clip_box, pl->block, pl->smem, &per_sm));
+    if (per_sm < 1) return fail(ctx, DOCK_ERR_UNSUPPORTED, "tile does not fit on an SM (%zu B shared)", pl->smem);
+    int want = (pl->ntask + pl->W - 1) / pl->W;
+    pl->grid = std::max(1, std::min(want, per_sm * ctx->num_sms));
+    FinalParams& F = pl->F;
+    F.pair0 = 0;
+    F.lig = P.lig;
+    F.pockets = P.pockets;
+    F.pose_key = P.pose_key;
+    F.pose_xyz = P.pose_xyz;
+    F.npairs = pl->npairs;
+    F.nlig = B.n;
+    F.natoms = B.natoms;
+    F.n_poses = N;
+    F.shift = k->score_mode == 0 ? 0.5f : 0.0f;
+    F.score = ctx->res.as<float>();
+    F.xyz_out = ctx->xyz_res.as<float>();
+    *out = pl.get();
+    ctx->plans[key] = std::move(pl);
+    return DOCK_OK;
+}
+
+// Enqueue one batched run: reset the queue, persistent sweep, finalize.
+int enqueue_batched(dock_ctx* ctx, Plan* pl, const dock_knobs* k, cudaStream_t s) {
+    CK(cudaMemsetAsync(ctx->counter.p, 0, sizeof(unsigned), s));
+    // external event records become event nodes when this is captured into a graph
+    CK(cudaEventRecordWithFlags(ctx->ev0, s, cudaEventRecordExternal));
+    if (pl->ntask > 0) CK(launch_sweep(pl->kc, pl->P, k->score_mode, k->clip_box, pl->grid, pl->block, pl->smem, s));
+    CK(cudaEventRecordWithFlags(ctx->ev1, s, cudaEventRecordExternal));
+    if (pl->npairs > 0) {
+        finalize_kernel<<<(pl->npairs + 3) / 4, 128, 0, s>>>(pl->F);
+        CK(cudaGetLastError());
+    }
+    return DOCK_OK;
+}
+
+// Plain comparison form: per (pocket, ligand) pair, its own queue reset,
+// sweep launch over that pair's pose groups, and finalize launch.
+int enqueue_plain(dock_ctx* ctx, Plan* pl, const dock_knobs* k, cudaStream_t s) {
+    const int G = 32 / pl->Q;
+    const int ngroup = (k->n_poses + G - 1) / G;
+    CK(cudaEventRecord(ctx->ev0, s));
+    for (int pair = 0; pair < pl->npairs; ++pair) {
+        SweepParams P = pl->P;
+        P.tasks = pl->P.tasks + (size_t)pair * ngroup;
+        P.ntask = ngroup;
+        int grid = (ngroup + pl->W - 1) / pl->W;
+        CK(cudaMemsetAsync(ctx->counter.p, 0, sizeof(unsigned), s));
+        CK(launch_sweep(pl->kc, P, k->score_mode, k->clip_box, grid, pl->block, pl->smem, s));
+        FinalParams F = pl->F;
+        F.pair0 = pair;
+        F.npairs = 1;
+        finalize_kernel<<<1, 32, 0, s>>>(F);
+        CK(cudaGetLastError());
+    }
+    CK(cudaEventRecord(ctx->ev1, s));
+    return DOCK_OK;
+}
+
+int check_run_args(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const dock_knobs* k) {
+    if (!ctx) return DOCK_ERR_INVALID_ARG;
+    if (batch_id < 0 || batch_id >= (int)ctx->batches.size() || !ctx->batches[batch_id].live)
+        return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_run: bad batch id");
+    if (np < 1 || !pids) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_run: no pockets");
+    for (int i = 0; i < np; ++i)
+        if (pids[i] < 0 || pids[i] >= (int)ctx->pockets.size() || !ctx->pockets[pids[i]].live)
+            return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_run: bad pocket id %d", pids[i]);
+    int rc = check_knobs(ctx, k);
+    if (rc) return rc;
+    int64_t pairs = (int64_t)np * ctx->batches[batch_id].n;
+    if (pairs * k->n_poses > (int64_t)1 << 31) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_run: too many poses");
+    return DOCK_OK;
+}
+
+void count_work(dock_ctx* ctx, const BatchH& B, int np, const dock_knobs* k, const Plan* pl, uint64_t launches) {
+    int P_hp = n_angles(k->hp_step), P_lp = n_angles(k->lp_step);
+    uint64_t cand = 0, upd = 0, bounds = 0, pairs = 0;
+    for (int b = 0; b < B.n; ++b)
+        for (int s = 0; s < B.nside[b]; ++s) {
+            int si = B.side_off[b] + s;
+            bool coarse = (double)B.side_m[si] / (double)B.l[b] <= k->threshold;
+            std::vector<int> phases{coarse ? P_lp - 1 : P_hp - 1};
+            if (k->enable_refinement && !coarse) {
+                int x = peel_tile(k->hp_step);
+                phases = {360 / x, (int)std::lround(x / k->hp_step)};
+            }
+            for (int nc : phases) {
+                int per_lane = (nc + pl->Q - 1) / pl->Q;
+                int chunks = (per_lane + pl->kc - 1) / pl->kc;
+                cand += nc;
+                upd += (uint64_t)nc * B.side_nmov[si];
+                // each lane of a pose tests its chunks' bounds; per pose that is Q lanes
+                bounds += (uint64_t)chunks * pl->Q * B.side_nmov[si] * B.side_nfixB[si];
+                pairs += (uint64_t)nc * B.side_nmov[si] * B.side_nfixB[si];
+            }
+        }
+    uint64_t mult = (uint64_t)np * k->n_poses * k->repetitions;
+    ctx->stats.candidates = cand * mult;
+    ctx->stats.atom_updates = upd * mult;
+    ctx->stats.pair_bounds = bounds * mult;
+    ctx->stats.bump_pairs = pairs * mult;
+    ctx->stats.kernel_launches = launches;
+    ctx->stats.sweep_ms = -1.0;
+    ctx->timed = true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dock_run(dock_ctx* ctx, int batch_id, const int32_t* pocket_ids, int npockets, const dock_knobs* k,
+             dock_result* out, float* xyz_out, int out_on_device, void* stream) {
+    int rc = check_run_args(ctx, batch_id, pocket_ids, npockets, k);
+    if (rc) return rc;
+    if (!out) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_run: NULL out");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    Plan* pl = nullptr;
+    if ((rc = get_plan(ctx, batch_id, pocket_ids, npockets, k, k->plain_mode, &pl))) return rc;
+    const BatchH& B = ctx->batches[batch_id];
+    uint64_t launches = 0;
+    if (k->plain_mode) {
+        if ((rc = enqueue_plain(ctx, pl, k, s))) return rc;
+        launches = 2ull * pl->npairs;
+    } else {
+        if (!pl->exec || pl->exec_stream != s) {
+            // capture the batched run once per plan and replay it
+            if (pl->exec) {
+                cudaGraphExecDestroy(pl->exec);
+                pl->exec = nullptr;
+            }
+            cudaStream_t cap = s;
+            cudaStream_t own = nullptr;
+            if (!cap) {
+                CK(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+                cap = own;
+            }
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+            int erc = enqueue_batched(ctx, pl, k, cap);
+            cudaError_t ce = cudaStreamEndCapture(cap, &g);
+            if (own) cudaStreamDestroy(own);
+            if (erc) {
+                if (g) cudaGraphDestroy(g);
+                return erc;
+            }
+            CK(ce);
+            cudaError_t ie = cudaGraphInstantiate(&pl->exec, g, 0);
+            cudaGraphDestroy(g);
+            CK(ie);
+            pl->exec_stream = s;
+        }
+        CK(cudaGraphLaunch(pl->exec, s));
+        launches = (pl->ntask > 0 ? 1 : 0) + (pl->npairs > 0 ? 1 : 0);
+    }
+    const size_t rbytes = (size_t)pl->npairs * sizeof(dock_result);
+    const size_t xbytes = (size_t)npockets * B.natoms * 3 * sizeof(float);
+    cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (rbytes) CK(cudaMemcpyAsync(out, ctx->res.p, rbytes, kind, s));
+    if (xyz_out && xbytes) CK(cudaMemcpyAsync(xyz_out, ctx->xyz_res.p, xbytes, kind, s));
+    if (!out_on_device) CK(cudaStreamSynchronize(s));
+    count_work(ctx, B, npockets, k, pl, launches);
+    return DOCK_OK;
+}
+
+int dock_run_trace(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs* k, const dock_trace* tr,
+                   dock_result* out, void* stream) {
+    int rc = check_run_args(ctx, batch_id, &pocket_id, 1, k);
+    if (rc) return rc;
+    if (!tr || !tr->chosen_k || !tr->cand_S || !tr->cand_status || !tr->pose_S || !tr->pose_init_S ||
+        !tr->pose_status || !tr->init_xyz || !tr->pose_xyz)
+        return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_run_trace: NULL trace buffer");
+    if (tr->pmax < trace_pmax(k)) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_run_trace: pmax too small");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    Plan* pl = nullptr;
+    int32_t pid = pocket_id;
+    if ((rc = get_plan(ctx, batch_id, &pid, 1, k, 0, &pl))) return rc;
+    SweepParams P = pl->P;
+    P.trace_on = 1;
+    P.tr.pmax = tr->pmax;
+    P.tr.chosen_k = tr->chosen_k;
+    P.tr.cand_S = tr->cand_S;
+    P.tr.cand_status = tr->cand_status;
+    P.tr.pose_S = tr->pose_S;
+    P.tr.pose_init_S = tr->pose_init_S;
+    P.tr.pose_status = tr->pose_status;
+    P.tr.init_xyz = tr->init_xyz;
+    P.tr.pose_xyz = tr->pose_xyz;
+    CK(cudaMemsetAsync(ctx->counter.p, 0, sizeof(unsigned), s));
+    if (pl->ntask > 0) CK(launch_sweep(pl->kc, P, k->score_mode, k->clip_box, pl->grid, pl->block, pl->smem, s));
+    if (pl->npairs > 0) {
+        finalize_kernel<<<(pl->npairs + 3) / 4, 128, 0, s>>>(pl->F);
+        CK(cudaGetLastError());
+    }
+    if (out && pl->npairs)
+        CK(cudaMemcpyAsync(out, ctx->res.p, (size_t)pl->npairs * sizeof(dock_result), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return DOCK_OK;
+}
+
+int dock_autotune(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs* k, dock_tile* best, void* stream) {
+    int32_t pid = pocket_id;
+    int rc = check_run_args(ctx, batch_id, &pid, 1, k);
+    if (rc) return rc;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const dock_tile saved = ctx->tile;
+    const std::string tkey = plan_key(batch_id, nullptr, 0, k, dock_tile{0, 0, 0}, 0);
+    ctx->tuned.erase(tkey);
+    std::vector<int> Qs;
+    for (int q : {1, 2, 4, 8})
+        if (32 / q <= 2 * k->n_poses || q == 8) Qs.push_back(q);
+    const int kcs[4] = {8, 12, 18, 36};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    dock_tile bt = default_tile(k);
+    for (int q : Qs)
+        for (int kc : kcs)
+            for (int w : {2, 4, 8}) {
+                dock_tile t{q, kc, w};
+                ctx->tile = t;
+                Plan* pl = nullptr;
+                if (get_plan(ctx, batch_id, &pid, 1, k, 0, &pl)) continue;
+                float ms = 0;
+                bool ok = true;
+                for (int rep = 0; rep < 2 && ok; ++rep) {  // first pass warms up
+                    cudaEventRecord(e0, s);
+                    ok = enqueue_batched(ctx, pl, k, s) == DOCK_OK;
+                    cudaEventRecord(e1, s);
+                    ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                }
+                if (ok && ms < best_ms) {
+                    best_ms = ms;
+                    bt = t;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tile = saved;
+    ctx->err.clear();
+    ctx->tuned[tkey] = bt;
+    if (best) *best = bt;
+    return DOCK_OK;
+}
+
+}  // extern "C"

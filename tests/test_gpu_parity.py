@@ -1,0 +1,199 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import parity
+import synth
+import synth.configs as C
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dk():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_06363_gb300 import Docker
+    d = Docker(0)
+    yield d
+    d.close()
+
+
+def _natoms(b):
+    return int(b.atom_off[-1])
+
+
+def trace_parity(dk, pk, batch, kn, opk=None, ids=None):
+    pid = dk.init_pocket(pk)
+    bid = dk.upload_ligands(batch, ids=ids)
+    g = dk.run_trace(bid, pid, kn, batch)
+    orc = parity.replay(opk or oracle.OraclePocket(pk), batch, kn, g, ids=ids)
+    stats = parity.check(batch, kn, g, orc)
+    parity.check_best(batch, kn, g["result"], g["pose_S"], g["pose_status"])
+    # the graph-captured batched run returns the trace run's results bit for bit
+    res, xyz = dk.run(bid, [pid], kn, batch.n, _natoms(batch))
+    assert np.array_equal(res.view(np.int32), g["result"].view(np.int32))
+    # best-pose coordinates are that pose's final coordinates
+    N = kn["n_poses"]
+    px = g["pose_xyz"].reshape(-1, 3)
+    for b in range(batch.n):
+        if res[b]["status"]:
+            continue
+        l = batch.atom_off[b + 1] - batch.atom_off[b]
+        o = batch.atom_off[b] * N + res[b]["pose"] * l
+        assert np.array_equal(xyz[0, batch.atom_off[b]:batch.atom_off[b + 1]], px[o:o + l])
+    dk.release_batch(bid)
+    return stats, g, res
+
+
+def test_field_bit_exact(dk):
+    pks = [C.single()[0][0], synth.pocket(8, 64, 0.5, C.ELLIPSOID), synth.pocket(9, 96, 0.5, (11, 9, 7))]
+    rng = np.random.default_rng(0)
+    pks.append(synth.Pocket((37, 23, 19), 0.4, (1.0, -2.0, 0.5), (5.0, 3.0, 4.0),
+                            np.stack([rng.integers(0, d, 50) for d in (37, 23, 19)], 1)))
+    for pk in pks:
+        pid = dk.init_pocket(pk)
+        assert np.array_equal(dk.pocket_field(pid, pk.dims), oracle.field(pk.dims, pk.pts))
+
+
+def test_single_ligand_config(dk):
+    pks, b, kn = C.single()
+    stats, g, res = trace_parity(dk, pks[0], b, kn)
+    assert stats["candidates"] > 1000
+    assert res[0]["status"] == 0 and res[0]["score"] > 0
+
+
+@pytest.mark.parametrize("n_poses", [40, 7])
+def test_small_batch_several_tiles(dk, n_poses):
+    # 40 poses: a full warp plus a ragged 8-pose tail; 7 poses: a partial warp
+    pk = synth.pocket(8, 64, 0.5, C.ELLIPSOID)
+    l, t = synth.ligand_sizes(11, 16, 0, [16, 64, 2, 12])
+    b = synth.ligand_batch(11, l, t)
+    kn = C.knobs(n_poses=n_poses, hp_step=15.0, lp_step=15.0, repetitions=2, seed=5)
+    stats, _, _ = trace_parity(dk, pk, b, kn)
+    assert stats["candidates"] > 10000
+
+
+def test_tile_shapes_bit_identical(dk):
+    pk = synth.pocket(8, 64, 0.5, C.ELLIPSOID)
+    l, t = synth.ligand_sizes(12, 24, 0, [16, 64, 2, 12])
+    b = synth.ligand_batch(12, l, t)
+    kn = C.knobs(n_poses=24, hp_step=10.0, lp_step=10.0, repetitions=1, seed=2)
+    pid = dk.init_pocket(pk)
+    bid = dk.upload_ligands(b)
+    ref = None
+    for q, kc, w in [(1, 12, 4), (1, 36, 4), (2, 18, 2), (4, 8, 8), (8, 8, 4), (1, 8, 1)]:
+        dk.set_tile(q, kc, w)
+        res, xyz = dk.run(bid, [pid], kn, b.n, _natoms(b))
+        if ref is None:
+            ref = (res.copy(), xyz.copy())
+        else:
+            assert np.array_equal(res.view(np.int32), ref[0].view(np.int32)), (q, kc, w)
+            assert np.array_equal(xyz, ref[1]), (q, kc, w)
+    dk.set_tile(0, 0, 0)
+    # plain one-launch-per-pair form: identical results
+    res, xyz = dk.run(bid, [pid], dict(kn, plain_mode=1), b.n, _natoms(b))
+    assert np.array_equal(res.view(np.int32), ref[0].view(np.int32))
+    assert np.array_equal(xyz, ref[1])
+    dk.release_batch(bid)
+
+
+@pytest.mark.parametrize("variant", ["threshold", "noclip", "peel", "trilinear", "trilinear_noclip", "reps0",
+                                     "step360"])
+def test_knob_variants(dk, variant):
+    n_grid = 40 if variant == "noclip" or variant == "trilinear_noclip" else 64
+    pk = synth.pocket(13, n_grid, 0.5, (6, 5, 4))
+    l, t = synth.ligand_sizes(13, 8, 0, [16, 48, 2, 8])
+    b = synth.ligand_batch(13, l, t)
+    kn = C.knobs(n_poses=12, hp_step=15.0, lp_step=15.0, repetitions=2, seed=3)
+    kn.update({
+        "threshold": dict(threshold=0.5, lp_step=45.0, hp_step=10.0),
+        "noclip": dict(clip_box=0),
+        "peel": dict(enable_refinement=1, hp_step=5.0, lp_step=30.0, threshold=0.3),
+        "trilinear": dict(score_mode=1),
+        "trilinear_noclip": dict(score_mode=1, clip_box=0),
+        "reps0": dict(repetitions=0),
+        "step360": dict(hp_step=360.0, lp_step=360.0),
+    }[variant])
+    trace_parity(dk, pk, b, kn)
+
+
+def test_edge_cases(dk):
+    pk = synth.pocket(14, 48, 0.5, C.ELLIPSOID)
+    pid = dk.init_pocket(pk)
+    kn = C.knobs(n_poses=5, repetitions=1, seed=1)
+    # empty batch
+    e = synth.LigandBatch(np.zeros(1, np.int32), np.zeros(1, np.int32), np.zeros(1, np.int32),
+                          np.zeros((0, 3), np.float32), np.zeros((0, 2), np.int32), np.zeros(0, np.int32))
+    bid = dk.upload_ligands(e)
+    res, xyz = dk.run(bid, [pid], kn, 0, 0)
+    assert len(res) == 0
+    # no rotatable bonds, a single atom, and a rotatable bond with a one-atom side
+    b0 = synth.ligand_batch(3, np.array([12, 9]), np.array([0, 0]))
+    one = synth.LigandBatch([0, 1], [0, 0], [0, 0], np.zeros((1, 3), np.float32), np.zeros((0, 2), np.int32),
+                            np.zeros(0, np.int32))
+    term = synth.ligand_batch(4, np.array([10]), np.array([0]))
+    leaf = int(np.nonzero(np.bincount(term.bonds.ravel(), minlength=10) == 1)[0][0])
+    e_leaf = int(np.nonzero((term.bonds == leaf).any(1))[0][0])
+    term = synth.LigandBatch(term.atom_off, term.bond_off, [0, 1], term.xyz, term.bonds, [e_leaf])
+    for batch in (b0, one, term):
+        trace_parity(dk, pk, batch, kn)
+    # every pose outside a tiny box: status 1
+    tiny = synth.Pocket((6, 6, 6), 0.5, (-1.25, -1.25, -1.25), (0, 0, 0), [[3, 3, 3]])
+    big = synth.ligand_batch(5, np.array([40]), np.array([4]))
+    _, g, res = trace_parity(dk, tiny, big, kn)
+    assert res[0]["status"] == 1 and res[0]["pose"] == -1 and res[0]["score"] == 0
+    # one pose
+    trace_parity(dk, pk, b0, dict(kn, n_poses=1))
+
+
+def test_error_paths(dk):
+    from paper_1901_06363_gb300 import DOCK_ERR_INVALID_ARG, DOCK_ERR_TOPOLOGY, DockError
+    pk = synth.pocket(14, 48, 0.5, C.ELLIPSOID)
+    pid = dk.init_pocket(pk)
+    b = synth.ligand_batch(3, np.array([12]), np.array([2]))
+    bid = dk.upload_ligands(b)
+    for bad in (dict(hp_step=0.5), dict(n_poses=0), dict(n_poses=5000), dict(repetitions=-1), dict(bump_thr=-1.0),
+                dict(score_mode=7)):
+        with pytest.raises(DockError) as ei:
+            dk.run(bid, [pid], C.knobs(**bad), b.n, _natoms(b))
+        assert ei.value.code == DOCK_ERR_INVALID_ARG
+    with pytest.raises(DockError) as ei:
+        dk.run(bid, [pid + 100], C.knobs(), b.n, _natoms(b))
+    assert ei.value.code == DOCK_ERR_INVALID_ARG
+    # a ring: the closing bond does not split the ligand
+    ring = synth.LigandBatch([0, 4], [0, 4], [0, 1], np.array([[0, 0, 0], [1.5, 0, 0], [1.5, 1.5, 0], [0, 1.5, 0]],
+                                                               np.float32),
+                             np.array([[0, 1], [1, 2], [2, 3], [3, 0]]), [1])
+    with pytest.raises(DockError) as ei:
+        dk.upload_ligands(ring)
+    assert ei.value.code == DOCK_ERR_TOPOLOGY
+    bad_atoms = synth.LigandBatch([0, 2], [0, 1], [0, 0], np.zeros((2, 3), np.float32), np.array([[0, 5]]),
+                                  np.zeros(0, np.int32))
+    with pytest.raises(DockError):
+        dk.upload_ligands(bad_atoms)
+
+
+def test_bench_workload_sampled(dk):
+    """1,024 ligands x 64^3 pocket, 64 poses, 10 degrees, 4 repetitions: the benchmark's launch, sampled."""
+    pks, b, kn = C.batched()
+    pid = dk.init_pocket(pks[0])
+    bid = dk.upload_ligands(b)
+    res, xyz = dk.run(bid, [pid], kn, b.n, _natoms(b))
+    assert np.all(res["status"] == 0) and np.all(res["score"] > 0)
+    # properties at full size: rigid geometry of every docked ligand is intact
+    for i in range(b.n):
+        a0, a1 = b.atom_off[i], b.atom_off[i + 1]
+        bonds = b.bonds[b.bond_off[i]:b.bond_off[i + 1]]
+        d0 = np.linalg.norm(b.xyz[a0:a1][bonds[:, 0]] - b.xyz[a0:a1][bonds[:, 1]], axis=1)
+        d1 = np.linalg.norm(xyz[0, a0:a1][bonds[:, 0]] - xyz[0, a0:a1][bonds[:, 1]], axis=1)
+        assert np.allclose(d0, d1, atol=2e-3)
+    # sampled ligands: the same ligands (same ids) traced alone give the same results, and replay against the oracle
+    sample = np.array([0, 17, 333, 511, 700, 1023])
+    sub = b.subset(sample)
+    opk = oracle.OraclePocket(pks[0])
+    _, g, res_sub = trace_parity(dk, pks[0], sub, kn, opk=opk, ids=sample)
+    assert np.array_equal(res_sub.view(np.int32), res[sample].view(np.int32))
+    dk.release_batch(bid)
