@@ -201,6 +201,13 @@ def run_ours(args):
     cand_per_step = st["candidates"]
     value = world * n * args.steps / total_s
 
+    if args.no_baselines:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": world * n * args.steps / total_s, "unit": UNIT,
+                              "sweep_ms": statistics.mean(sweep_ms), "note": "timed steps only"}), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
     # end to end through the C ABI with host buffers: upload (H2D), dock, results back (D2H)
     e2e_steps = max(2, min(args.steps, 5))
     res_host = None
@@ -278,6 +285,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-baselines", action="store_true",
+                    help="skip the CPU oracle, end-to-end and plain-form legs (for profiling the timed steps)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
