@@ -264,6 +264,37 @@ typedef struct {
 
 int dock_last_stats(const dock_ctx* ctx, dock_stats* s);
 
+/* dock_run for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart: this exists for the library's users. Some
+ * callers must not call cudaMalloc or cudaFree on the docking path: a
+ * serving loop whose device memory is carved up in advance by its own pool
+ * or arena and is capped there, or a caller that cannot afford the device
+ * synchronisation an allocation or a free may bring. dock_run may allocate
+ * its scratch on first use or when a batch grows; this call never does. Its
+ * scratch (work-queue head, angle tables, pocket descriptor, task list,
+ * per-pose keys and coordinates) lives in one file-scope device array of
+ * about 50 MiB, which every GPU that loads the library holds until the
+ * process exits.
+ *
+ * Same docking as dock_run on ONE pocket, same results; the batch and pocket
+ * must already be uploaded (dock_upload_ligands and dock_init_pocket do
+ * allocate; do them at set-up). Outputs are device memory, written in stream
+ * order on `stream`; the call does not wait for them.
+ *   out      device array of n dock_result (n = ligands in the batch)
+ *   xyz_out  NULL or device array of 3*atom_off[n] floats (best pose, Å)
+ * Limits per call: n_poses * n <= 131072 and n_poses * atom_off[n] <=
+ * 4194304, and at most 361 angles per sweep; larger runs fail with
+ * DOCK_ERR_INVALID_ARG before anything is launched.
+ * The first call on a device looks up the array's device address there (once
+ * per device, with that device current); make that first call before any
+ * stream capture. Every call shares the one array and leaves its contents
+ * behind: the call clears what must start at zero itself, and calls whose
+ * work overlaps on the GPU (other streams, other threads) race on it; keep
+ * them ordered. dock_last_stats is not updated by this call. */
+int dock_run_static(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs* k, dock_result* out,
+                    float* xyz_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

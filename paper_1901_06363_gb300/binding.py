@@ -90,6 +90,7 @@ def _load():
         "dock_get_tile": ([vp, P(dock_tile)], ctypes.c_int),
         "dock_autotune": ([vp, ctypes.c_int, ctypes.c_int, P(dock_knobs), P(dock_tile), vp], ctypes.c_int),
         "dock_last_stats": ([vp, P(dock_stats)], ctypes.c_int),
+        "dock_run_static": ([vp, ctypes.c_int, ctypes.c_int, P(dock_knobs), vp, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

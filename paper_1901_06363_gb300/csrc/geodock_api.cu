@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <memory>
 #include <numeric>
 #include <string>
@@ -882,3 +883,179 @@ int dock_autotune(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs* 
 }
 
 }  // extern "C"
+
+// ======================================================== static-scratch run
+//
+// dock_run_static: the batched sweep with its scratch (work-queue head, angle
+// tables, pocket descriptor, task list, per-pose keys and coordinates) taken
+// from one file-scope device array instead of allocated memory. The array is
+// created when the library's module is loaded on a device and held there
+// until the process exits, whether or not this entry point is ever called.
+
+namespace {
+
+constexpr int64_t kStaticPoseSlots = int64_t(1) << 17;  // (ligand, pose) slots per call
+constexpr int64_t kStaticAtomPoses = int64_t(1) << 22;  // (atom, pose) slots per call
+constexpr int kStaticAngles = 361;                       // angles per table (1 degree steps and up)
+
+constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t kOffCounter = 0;
+constexpr size_t kOffPocket = 256;
+constexpr size_t kOffTables = kOffPocket + align256(sizeof(PocketDev));
+constexpr size_t kOffTasks = kOffTables + align256(3 * kStaticAngles * sizeof(float2));
+constexpr size_t kOffKeys = kOffTasks + align256(kStaticPoseSlots * sizeof(int2));
+constexpr size_t kOffXyz = kOffKeys + align256(kStaticPoseSlots * sizeof(unsigned long long));
+constexpr size_t kStaticBytes = kOffXyz + align256(kStaticAtomPoses * 3 * sizeof(float));  // about 50 MiB
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_dock_scratch[kStaticBytes];
+
+namespace {
+
+// Device address of g_dock_scratch on each device, looked up once per device
+// (with that device current) on the first call there.
+std::mutex g_static_mu;
+void* g_static_addr[256] = {};
+
+cudaError_t static_scratch(int device, unsigned char** out) {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (device < 0 || device >= 256) return cudaErrorInvalidDevice;
+    if (!g_static_addr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_dock_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_addr[device] = p;
+    }
+    *out = static_cast<unsigned char*>(g_static_addr[device]);
+    return cudaSuccess;
+}
+
+// Work list in (pocket-ligand pair, pose group) order.
+__global__ void static_tasks_kernel(int2* tasks, int npairs, int ngroup) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < (int64_t)npairs * ngroup) tasks[t] = make_int2((int)(t / ngroup), (int)(t % ngroup));
+}
+
+// cos/sin of the angles offset + i * stride (degrees), FP64 rounded to FP32.
+void fill_table(float2* t, int n, double offset, double stride) {
+    const double rad = 3.14159265358979323846 / 180.0;
+    for (int i = 0; i < n; ++i) {
+        double a = offset + i * stride;
+        t[i] = make_float2((float)std::cos(a * rad), (float)std::sin(a * rad));
+    }
+}
+
+}  // namespace
+
+extern "C" int dock_run_static(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs* k, dock_result* out,
+                               float* xyz_out, void* stream) {
+    int32_t pid = pocket_id;
+    int rc = check_run_args(ctx, batch_id, &pid, 1, k);
+    if (rc) return rc;
+    if (!out) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_run_static: NULL out");
+    CK(cudaSetDevice(ctx->device));
+    const BatchH& B = ctx->batches[batch_id];
+    const int N = k->n_poses;
+    const int64_t pose_slots = (int64_t)B.n * N, atom_poses = (int64_t)B.natoms * N;
+    if (pose_slots > kStaticPoseSlots || atom_poses > kStaticAtomPoses)
+        return fail(ctx, DOCK_ERR_INVALID_ARG,
+                    "dock_run_static: %lld ligand-poses and %lld atom-poses exceed the static scratch "
+                    "(at most %lld and %lld per call); split the batch or use dock_run",
+                    (long long)pose_slots, (long long)atom_poses, (long long)kStaticPoseSlots,
+                    (long long)kStaticAtomPoses);
+    const int P_hp = n_angles(k->hp_step), P_lp = n_angles(k->lp_step);
+    int n_tiles = 0, per_tile = 0, tile = 0;
+    if (k->enable_refinement) {
+        tile = peel_tile(k->hp_step);
+        n_tiles = 360 / tile;
+        per_tile = (int)std::lround(tile / k->hp_step);
+    }
+    if (P_hp > kStaticAngles || P_lp > kStaticAngles || n_tiles > kStaticAngles)
+        return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_run_static: too many angles per sweep");
+    unsigned char* base = nullptr;
+    CK(static_scratch(ctx->device, &base));
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // tile shape: the forced fields of dock_set_tile over the default (results do not depend on it)
+    dock_tile t = default_tile(k);
+    if (ctx->tile.lanes_per_pose) t.lanes_per_pose = ctx->tile.lanes_per_pose;
+    if (ctx->tile.angles_per_chunk) t.angles_per_chunk = ctx->tile.angles_per_chunk;
+    if (ctx->tile.warps_per_cta) t.warps_per_cta = ctx->tile.warps_per_cta;
+    const int Q = t.lanes_per_pose, G = 32 / Q, W = t.warps_per_cta, block = 32 * W;
+    const int ngroup = (N + G - 1) / G;
+    const int ntask = B.n * ngroup;
+    const size_t smem = (size_t)W * B.lmax * 3 * G * sizeof(float);
+    int per_sm = 0;
+    CK(occupancy(t.angles_per_chunk, k->score_mode, k->clip_box, block, smem, &per_sm));
+    if (per_sm < 1) return fail(ctx, DOCK_ERR_UNSUPPORTED, "dock_run_static: tile does not fit on an SM");
+
+    // angle tables and the pocket descriptor: host values copied into the array
+    float2 tabs[3][kStaticAngles];
+    fill_table(tabs[0], P_hp, 0.0, k->hp_step);
+    fill_table(tabs[1], P_lp, 0.0, k->lp_step);
+    if (n_tiles) fill_table(tabs[2], n_tiles, 0.5 * tile, (double)tile);
+    else tabs[2][0] = make_float2(1.f, 0.f);
+    const PocketDev pd = ctx->pockets[pocket_id].d;
+    CK(cudaMemcpyAsync(base + kOffTables, tabs, sizeof tabs, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(base + kOffPocket, &pd, sizeof pd, cudaMemcpyHostToDevice, s));
+    // the queue head must start at zero; every other word is written before it is read
+    CK(cudaMemsetAsync(base + kOffCounter, 0, sizeof(unsigned), s));
+    if (ntask > 0) {
+        static_tasks_kernel<<<(ntask + 255) / 256, 256, 0, s>>>(reinterpret_cast<int2*>(base + kOffTasks), B.n, ngroup);
+        CK(cudaGetLastError());
+    }
+
+    SweepParams P{};
+    P.lig = B.lig->as<LigDev>();
+    P.side = B.side->as<SideDev>();
+    P.idx = B.idx->as<uint8_t>();
+    P.xyz0 = B.xyz0->as<float>();
+    P.pockets = reinterpret_cast<const PocketDev*>(base + kOffPocket);
+    P.tasks = reinterpret_cast<const int2*>(base + kOffTasks);
+    P.ntask = ntask;
+    P.nlig = B.n;
+    P.natoms = B.natoms;
+    P.counter = reinterpret_cast<unsigned*>(base + kOffCounter);
+    P.n_poses = N;
+    P.repetitions = k->repetitions;
+    P.Q = Q;
+    P.lmax = B.lmax;
+    P.threshold = k->threshold;
+    P.bump_thr = k->bump_thr;
+    P.seed = k->seed;
+    const float2* tab = reinterpret_cast<const float2*>(base + kOffTables);
+    P.cs_hp = tab;
+    P.cs_lp = tab + kStaticAngles;
+    P.P_hp = P_hp;
+    P.P_lp = P_lp;
+    P.peel = k->enable_refinement ? 1 : 0;
+    P.cs_peel = tab + 2 * kStaticAngles;
+    P.n_tiles = n_tiles;
+    P.per_tile = per_tile;
+    P.pose_key = reinterpret_cast<unsigned long long*>(base + kOffKeys);
+    P.pose_xyz = reinterpret_cast<float*>(base + kOffXyz);
+    P.trace_on = 0;
+    if (ntask > 0) {
+        const int grid = std::max(1, std::min((ntask + W - 1) / W, per_sm * ctx->num_sms));
+        CK(launch_sweep(t.angles_per_chunk, P, k->score_mode, k->clip_box, grid, block, smem, s));
+    }
+    if (B.n > 0) {
+        FinalParams F{};
+        F.pair0 = 0;
+        F.lig = P.lig;
+        F.pockets = P.pockets;
+        F.pose_key = P.pose_key;
+        F.pose_xyz = P.pose_xyz;
+        F.npairs = B.n;
+        F.nlig = B.n;
+        F.natoms = B.natoms;
+        F.n_poses = N;
+        F.shift = k->score_mode == 0 ? 0.5f : 0.0f;
+        F.score = reinterpret_cast<float*>(out);
+        F.xyz_out = xyz_out;
+        finalize_kernel<<<(B.n + 3) / 4, 128, 0, s>>>(F);
+        CK(cudaGetLastError());
+    }
+    return DOCK_OK;
+}
