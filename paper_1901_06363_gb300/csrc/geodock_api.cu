@@ -52,7 +52,7 @@ struct DevBuf {
 struct PocketH {
     bool live = false;
     PocketDev d{};
-    std::unique_ptr<DevBuf> K;
+    std::unique_ptr<DevBuf> K, Kp;
 };
 
 struct BatchH {
@@ -67,7 +67,8 @@ struct BatchH {
 
 // Everything a batched run needs that depends on (batch, pockets, knobs, tile).
 struct Plan {
-    int ntask = 0, npairs = 0;
+    int ntask = 0, npairs = 0, slice = 0;
+    std::vector<int> task_off;  // first task of each pair (plain form: pair order)
     std::unique_ptr<DevBuf> tasks, pockets, cs_hp, cs_lp, cs_peel;
     SweepParams P{};
     FinalParams F{};
@@ -179,16 +180,50 @@ int trace_pmax(const dock_knobs* k) {
     return p;
 }
 
-// Default tile shape: lanes per pose so that a warp holds no more poses than
-// the run has, and angles per chunk to cover a hp sweep in few chunks.
+// Default tile shape. lanes_per_pose applies to ligands of up to 32 atoms
+// (larger ligands double it per doubling of size, see lanes_log2): chosen so a
+// warp holds no more poses than the run has. angles_per_chunk covers a hp
+// sweep in few chunks.
 dock_tile default_tile(const dock_knobs* k) {
     dock_tile t;
     int N = k->n_poses;
     t.lanes_per_pose = N >= 32 ? 1 : (N >= 16 ? 2 : (N >= 8 ? 4 : 8));
-    int per_lane = (n_angles(k->hp_step) - 1 + t.lanes_per_pose - 1) / t.lanes_per_pose;
-    t.angles_per_chunk = per_lane <= 8 ? 8 : (per_lane <= 12 ? 12 : (per_lane <= 18 ? 18 : 36));
-    t.warps_per_cta = 4;
+    int ncand = n_angles(k->hp_step) - 1;
+    t.angles_per_chunk = ncand <= 8 ? 8 : (ncand <= 12 ? 12 : (ncand <= 18 ? 18 : 36));
+    t.warps_per_cta = t.angles_per_chunk == 36 ? 8 : 4;
     return t;
+}
+
+// Shared-memory floats per warp for its poses' coordinates: 32 atoms of
+// 32 / lanes_per_pose poses (never more than the batch needs).
+int slice_floats(const dock_tile& t, int lmax) {
+    return ((32 / t.lanes_per_pose) * std::min(32, lmax) * 3 + 3) & ~3;  // 16-byte multiple
+}
+
+// log2 of the lanes per pose for a ligand of l atoms: the smallest Q >= the
+// tile's lanes_per_pose with (32/Q) poses x l atoms inside the warp's slice.
+int lanes_log2(const dock_tile& t, int slice, int l) {
+    int lq = 0;
+    while ((1 << lq) < t.lanes_per_pose) ++lq;
+    while (lq < 5 && (32 >> lq) * l * 3 > slice) ++lq;
+    return lq;
+}
+
+// Shared memory of a CTA: per warp the coordinate slice, the bump list and
+// the chunk's angle table.
+size_t cta_smem(const dock_tile& t, int slice, int bw) {
+    return (size_t)t.warps_per_cta * (slice + warp_extra_floats(t.angles_per_chunk, bw)) * sizeof(float);
+}
+
+// 64-bit bump words per lane: the largest phase of a sweep (flat hp or lp
+// sweep, tile centres, or one tile's angles) in 64-candidate words.
+int bump_words(const dock_knobs* k) {
+    int m = std::max(n_angles(k->hp_step), n_angles(k->lp_step)) - 1;
+    if (k->enable_refinement) {
+        int x = peel_tile(k->hp_step);
+        m = std::max(m, std::max(360 / x, (int)std::lround(x / k->hp_step)));
+    }
+    return std::max(1, (m + 63) / 64);
 }
 
 cudaError_t launch_sweep(int kc, const SweepParams& P, int mode, int clip, int grid, int block, size_t smem,
@@ -232,11 +267,11 @@ double task_cost(const BatchH& B, int b, const dock_knobs* k, int Q, int kc) {
             int x = peel_tile(k->hp_step);
             ncand = 360 / x + (int)std::lround(x / k->hp_step);
         }
-        int per_lane = (ncand + Q - 1) / Q;
-        int chunks = (per_lane + kc - 1) / kc;
-        c += (double)B.side_nmov[si] * (chunks * kc * 1.0 + chunks * B.side_nfixB[si] * 0.6) + B.l[b];
+        int chunks = (ncand + kc - 1) / kc;
+        int nslot = (B.side_nmov[si] + Q - 1) / Q;
+        c += (double)nslot * (chunks * (kc * 15.0 + 25.0) + B.side_nfixB[si] * 7.0) + 40.0 * B.l[b] / Q;
     }
-    return c * std::max(k->repetitions, 1) + B.l[b] * 4.0;
+    return c * std::max(k->repetitions, 1) + B.l[b] * 20.0 / Q;
 }
 
 }  // namespace
@@ -308,7 +343,18 @@ int dock_init_pocket(dock_ctx* ctx, const dock_pocket* p, int* pocket_id) {
         CK(cudaGetLastError());
         CK(cudaDeviceSynchronize());
     }
+    // padded 32-bit copy used by the sweep's unchecked lookups
+    {
+        const int64_t np = (int64_t)(p->nx + 2 * PAD) * (p->ny + 2 * PAD) * (p->nz + 2 * PAD);
+        ph.Kp.reset(new DevBuf());
+        CK(ph.Kp->ensure(np * sizeof(uint32_t)));
+        pad_field_kernel<<<(unsigned)((np + 255) / 256), 256>>>(ph.Kp->as<uint32_t>(), ph.K->as<uint16_t>(), p->nx,
+                                                                p->ny, p->nz);
+        CK(cudaGetLastError());
+        CK(cudaDeviceSynchronize());
+    }
     ph.d.K = ph.K->as<uint16_t>();
+    ph.d.Kp = ph.Kp->as<uint32_t>();
     ph.d.nx = p->nx;
     ph.d.ny = p->ny;
     ph.d.nz = p->nz;
@@ -538,9 +584,8 @@ int get_plan(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const doc
     pl->kc = t.angles_per_chunk;
     pl->W = t.warps_per_cta;
     pl->block = 32 * pl->W;
-    const int G = 32 / pl->Q;
+    pl->slice = slice_floats(t, B.lmax);
     const int N = k->n_poses;
-    const int ngroup = (N + G - 1) / G;
     pl->npairs = np * B.n;
     // pockets
     std::vector<PocketDev> pd(np);
@@ -567,15 +612,19 @@ int get_plan(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const doc
     // tasks: (pair, pose group); batched form in descending cost (longest first),
     // plain form in pair order
     std::vector<int2> tasks;
-    tasks.reserve((size_t)pl->npairs * ngroup);
     std::vector<double> cost;
+    pl->task_off.assign(pl->npairs + 1, 0);
     for (int pk = 0; pk < np; ++pk)
         for (int b = 0; b < B.n; ++b) {
-            double c = task_cost(B, b, k, pl->Q, pl->kc);
+            const int lq = lanes_log2(t, pl->slice, B.l[b]);
+            const int G = 32 >> lq;
+            const int ngroup = (N + G - 1) / G;
+            double c = task_cost(B, b, k, 1 << lq, pl->kc);
             for (int g = 0; g < ngroup; ++g) {
-                tasks.push_back(make_int2(pk * B.n + b, g));
+                tasks.push_back(make_int2(pk * B.n + b, g | (lq << 16)));
                 cost.push_back(c);
             }
+            pl->task_off[pk * B.n + b + 1] = (int)tasks.size();
         }
     if (!plain) {
         std::vector<int> order(tasks.size());
@@ -615,8 +664,7 @@ int get_plan(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const doc
     P.counter = ctx->counter.as<unsigned>();
     P.n_poses = N;
     P.repetitions = k->repetitions;
-    P.Q = pl->Q;
-    P.lmax = B.lmax;
+    P.slice = pl->slice;
     P.threshold = k->threshold;
     P.bump_thr = k->bump_thr;
     P.seed = k->seed;
@@ -625,13 +673,17 @@ int get_plan(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const doc
     P.P_hp = P_hp;
     P.P_lp = P_lp;
     P.peel = k->enable_refinement ? 1 : 0;
+    P.hp_step = (float)k->hp_step;
+    P.lp_step = (float)k->lp_step;
+    P.tile = k->enable_refinement ? (float)peel_tile(k->hp_step) : 0.f;
     P.cs_peel = pl->cs_peel->as<float2>();
     P.n_tiles = n_tiles;
     P.per_tile = per_tile;
     P.pose_key = ctx->pose_key.as<unsigned long long>();
     P.pose_xyz = ctx->pose_xyz.as<float>();
     P.trace_on = 0;
-    pl->smem = (size_t)pl->W * B.lmax * 3 * G * sizeof(float);
+    P.bw = bump_words(k);
+    pl->smem = cta_smem(t, pl->slice, P.bw);
     int per_sm = 0;
     CK(occupancy(pl->kc, k->score_mode, k->clip_box, pl->block, pl->smem, &per_sm));
     if (per_sm < 1) return fail(ctx, DOCK_ERR_UNSUPPORTED, "tile does not fit on an SM (%zu B shared)", pl->smem);
@@ -672,12 +724,11 @@ int enqueue_batched(dock_ctx* ctx, Plan* pl, const dock_knobs* k, cudaStream_t s
 // Plain comparison form: per (pocket, ligand) pair, its own queue reset,
 // sweep launch over that pair's pose groups, and finalize launch.
 int enqueue_plain(dock_ctx* ctx, Plan* pl, const dock_knobs* k, cudaStream_t s) {
-    const int G = 32 / pl->Q;
-    const int ngroup = (k->n_poses + G - 1) / G;
     CK(cudaEventRecord(ctx->ev0, s));
     for (int pair = 0; pair < pl->npairs; ++pair) {
         SweepParams P = pl->P;
-        P.tasks = pl->P.tasks + (size_t)pair * ngroup;
+        const int ngroup = pl->task_off[pair + 1] - pl->task_off[pair];
+        P.tasks = pl->P.tasks + pl->task_off[pair];
         P.ntask = ngroup;
         int grid = (ngroup + pl->W - 1) / pl->W;
         CK(cudaMemsetAsync(ctx->counter.p, 0, sizeof(unsigned), s));
@@ -720,14 +771,12 @@ void count_work(dock_ctx* ctx, const BatchH& B, int np, const dock_knobs* k, con
                 phases = {360 / x, (int)std::lround(x / k->hp_step)};
             }
             for (int nc : phases) {
-                int per_lane = (nc + pl->Q - 1) / pl->Q;
-                int chunks = (per_lane + pl->kc - 1) / pl->kc;
                 cand += nc;
                 upd += (uint64_t)nc * B.side_nmov[si];
-                // each lane of a pose tests its chunks' bounds; per pose that is Q lanes
-                bounds += (uint64_t)chunks * pl->Q * B.side_nmov[si] * B.side_nfixB[si];
                 pairs += (uint64_t)nc * B.side_nmov[si] * B.side_nfixB[si];
             }
+            // the circle bound tests every pair once per sweep
+            bounds += (uint64_t)B.side_nmov[si] * B.side_nfixB[si];
         }
     uint64_t mult = (uint64_t)np * k->n_poses * k->repetitions;
     ctx->stats.candidates = cand * mult;
@@ -931,10 +980,11 @@ cudaError_t static_scratch(int device, unsigned char** out) {
     return cudaSuccess;
 }
 
-// Work list in (pocket-ligand pair, pose group) order.
-__global__ void static_tasks_kernel(int2* tasks, int npairs, int ngroup) {
+// Work list in (pocket-ligand pair, pose group) order, one lanes-per-pose
+// (2^lq) for the whole batch.
+__global__ void static_tasks_kernel(int2* tasks, int npairs, int ngroup, int lq) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < (int64_t)npairs * ngroup) tasks[t] = make_int2((int)(t / ngroup), (int)(t % ngroup));
+    if (t < (int64_t)npairs * ngroup) tasks[t] = make_int2((int)(t / ngroup), (int)(t % ngroup) | (lq << 16));
 }
 
 // cos/sin of the angles offset + i * stride (degrees), FP64 rounded to FP32.
@@ -982,10 +1032,13 @@ extern "C" int dock_run_static(dock_ctx* ctx, int batch_id, int pocket_id, const
     if (ctx->tile.lanes_per_pose) t.lanes_per_pose = ctx->tile.lanes_per_pose;
     if (ctx->tile.angles_per_chunk) t.angles_per_chunk = ctx->tile.angles_per_chunk;
     if (ctx->tile.warps_per_cta) t.warps_per_cta = ctx->tile.warps_per_cta;
-    const int Q = t.lanes_per_pose, G = 32 / Q, W = t.warps_per_cta, block = 32 * W;
+    const int slice = slice_floats(t, B.lmax);
+    const int lq = lanes_log2(t, slice, B.lmax);  // sized for the largest ligand
+    const int G = 32 >> lq, W = t.warps_per_cta, block = 32 * W;
     const int ngroup = (N + G - 1) / G;
     const int ntask = B.n * ngroup;
-    const size_t smem = (size_t)W * B.lmax * 3 * G * sizeof(float);
+    const int bw = bump_words(k);
+    const size_t smem = cta_smem(t, slice, bw);
     int per_sm = 0;
     CK(occupancy(t.angles_per_chunk, k->score_mode, k->clip_box, block, smem, &per_sm));
     if (per_sm < 1) return fail(ctx, DOCK_ERR_UNSUPPORTED, "dock_run_static: tile does not fit on an SM");
@@ -1002,7 +1055,8 @@ extern "C" int dock_run_static(dock_ctx* ctx, int batch_id, int pocket_id, const
     // the queue head must start at zero; every other word is written before it is read
     CK(cudaMemsetAsync(base + kOffCounter, 0, sizeof(unsigned), s));
     if (ntask > 0) {
-        static_tasks_kernel<<<(ntask + 255) / 256, 256, 0, s>>>(reinterpret_cast<int2*>(base + kOffTasks), B.n, ngroup);
+        static_tasks_kernel<<<(ntask + 255) / 256, 256, 0, s>>>(reinterpret_cast<int2*>(base + kOffTasks), B.n, ngroup,
+                                                                lq);
         CK(cudaGetLastError());
     }
 
@@ -1019,8 +1073,8 @@ extern "C" int dock_run_static(dock_ctx* ctx, int batch_id, int pocket_id, const
     P.counter = reinterpret_cast<unsigned*>(base + kOffCounter);
     P.n_poses = N;
     P.repetitions = k->repetitions;
-    P.Q = Q;
-    P.lmax = B.lmax;
+    P.slice = slice;
+    P.bw = bw;
     P.threshold = k->threshold;
     P.bump_thr = k->bump_thr;
     P.seed = k->seed;
@@ -1030,6 +1084,9 @@ extern "C" int dock_run_static(dock_ctx* ctx, int batch_id, int pocket_id, const
     P.P_hp = P_hp;
     P.P_lp = P_lp;
     P.peel = k->enable_refinement ? 1 : 0;
+    P.hp_step = (float)k->hp_step;
+    P.lp_step = (float)k->lp_step;
+    P.tile = (float)tile;
     P.cs_peel = tab + 2 * kStaticAngles;
     P.n_tiles = n_tiles;
     P.per_tile = per_tile;

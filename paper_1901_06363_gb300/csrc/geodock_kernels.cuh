@@ -33,8 +33,16 @@ namespace gd {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// Margin (voxels) of the padded copy of the field: cells outside the grid
+// hold OUTSIDE, so a sum over atoms is >= OUTSIDE exactly when one of them
+// lies outside the box (255 atoms x 2^24 < 2^32, and sums of in-box values
+// stay below 255 x 65535 < 2^24).
+constexpr int PAD = 16;
+constexpr uint32_t OUTSIDE = 1u << 24;
+
 struct PocketDev {
-    const uint16_t* K;  // floored field, x fastest
+    const uint16_t* K;   // floored field, x fastest
+    const uint32_t* Kp;  // the same values padded by PAD voxels per side, OUTSIDE beyond the grid
     int nx, ny, nz;
     double h;  // voxel edge (Å)
     double origin[3];
@@ -77,15 +85,15 @@ struct SweepParams {
     const uint8_t* idx;
     const float* xyz0;  // input coordinates, 3 per atom (Å)
     const PocketDev* pockets;
-    const int2* tasks;  // (pair, pose group); pair = pocket * nlig + ligand
+    const int2* tasks;  // (pair, group | log2(lanes per pose) << 16); pair = pocket * nlig + ligand
     int ntask;
+    int slice;           // floats of shared memory per warp for its poses' coordinates
+    int bw;              // 64-bit bump words per lane (ceil of the largest phase / 64)
     int nlig;
     int natoms;          // atoms in the batch
     unsigned* counter;   // work queue head (scratch, zeroed before launch)
     int n_poses;
     int repetitions;
-    int Q;               // lanes per pose
-    int lmax;            // largest ligand of the batch (shared-memory stride)
     double threshold;
     double bump_thr;     // Å
     uint64_t seed;
@@ -93,6 +101,7 @@ struct SweepParams {
     const float2* cs_lp;
     int P_hp, P_lp;
     // tile peeling
+    float hp_step, lp_step, tile;  // degrees
     int peel;            // 1: hp sweeps use tile peeling
     const float2* cs_peel;  // cos/sin of the tile centres
     int n_tiles;         // 360 / tile
@@ -136,6 +145,18 @@ __device__ __forceinline__ Split split(float3 x, float3 c, float3 k) {
     s.w = make_float3(__fmaf_rn(k.y, s.u.z, -__fmul_rn(k.z, s.u.y)), __fmaf_rn(k.z, s.u.x, -__fmul_rn(k.x, s.u.z)),
                       __fmaf_rn(k.x, s.u.y, -__fmul_rn(k.y, s.u.x)));
     return s;
+}
+// The same circle with its angle origin turned by r = (cos, sin): the
+// candidate at angle phi of the result is the one at angle (origin + phi) of
+// s. r = (1, 0) leaves s unchanged bit for bit.
+__device__ __forceinline__ Split turn(const Split& s, float2 r) {
+    Split o;
+    o.a = s.a;
+    o.u = make_float3(__fmaf_rn(r.y, s.w.x, __fmul_rn(r.x, s.u.x)), __fmaf_rn(r.y, s.w.y, __fmul_rn(r.x, s.u.y)),
+                      __fmaf_rn(r.y, s.w.z, __fmul_rn(r.x, s.u.z)));
+    o.w = make_float3(__fmaf_rn(r.x, s.w.x, -__fmul_rn(r.y, s.u.x)), __fmaf_rn(r.x, s.w.y, -__fmul_rn(r.y, s.u.y)),
+                      __fmaf_rn(r.x, s.w.z, -__fmul_rn(r.y, s.u.z)));
+    return o;
 }
 __device__ __forceinline__ float3 place(const Split& s, float cs, float sn) {
     return make_float3(__fmaf_rn(sn, s.w.x, __fmaf_rn(cs, s.u.x, s.a.x)),
@@ -242,89 +263,167 @@ __device__ __forceinline__ unsigned long long make_key(float S, int k) {
 
 // ------------------------------------------------------------- sweep kernel
 
-// One pass over a chunk of up to KC candidate angles of one fragment sweep,
-// for the lane's pose. Returns the best (S, slot) key among the chunk's
-// feasible candidates, or ~0.
-template <int KC, int MODE, bool CLIP>
-__device__ __forceinline__ unsigned long long sweep_chunk(const PocketDev& pd, const uint16_t* __restrict__ K,
-                                                          const float* xs, int G, int ps,
-                                                          const uint8_t* __restrict__ mov, int nmov,
-                                                          const uint8_t* __restrict__ fixB, int nfixB, float3 gc,
-                                                          float3 kax, float thr_g, float S_fix, bool live,
-                                                          const float2 (&csj)[KC], int slot_start, int slot_step,
-                                                          int nvalid, float* trace_S, int* trace_st) {
-    float cj[KC], sj[KC];
-#pragma unroll
-    for (int j = 0; j < KC; ++j) {
-        cj[j] = csj[j].x;
-        sj[j] = csj[j].y;
-    }
-    float acc[KC];
-#pragma unroll
-    for (int j = 0; j < KC; ++j) acc[j] = 0.f;
-    unsigned long long bad = 0ull, box = 0ull;
-    const float thr2 = thr_g * thr_g;
+// Infeasible-candidate bits of one sweep phase, per lane: up to BW 64-bit
+// words (448 candidates), lane-interleaved after the warp's coordinates; a
+// run uses bw = ceil(largest phase / 64) of them.
+constexpr int BW = 7;
+// Besides its coordinate slice a warp keeps in shared memory only the bump
+// bits (bw words per lane) and the chunk's angles: the rest of the SM's
+// shared memory serves as L1 cache for the field lookups.
+__host__ __device__ constexpr int warp_extra_floats(int kc, int bw) { return bw * 64 + 2 * kc; }
 
-    for (int im = 0; im < nmov; ++im) {
-        const int i = mov[im];
-        Split s = split(ld3(xs, i, G, ps), gc, kax);
+// 32-bit sums over the Q lanes of a pose.
+__device__ __forceinline__ uint32_t group_add_u(uint32_t v, int Q) {
+    for (int off = Q >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+    return v;
+}
+template <class M>
+__device__ __forceinline__ M group_or(M v, int Q) {
+    for (int off = Q >> 1; off > 0; off >>= 1) v |= __shfl_xor_sync(FULL, v, off);
+    return v;
+}
+
+// Accumulator of one candidate: exact integers in nearest mode, floats in trilinear mode.
+template <int MODE>
+struct Acc {
+    using T = uint32_t;
+};
+template <>
+struct Acc<1> {
+    using T = float;
+};
+
+// Value of the padded field at padded shifted position t (nearest mode), for
+// a position known to lie inside the padded box: floor by the
+// round-toward-zero trick, no bounds test. bias folds the 2^23 offsets.
+__device__ __forceinline__ uint32_t lookup_padded(const uint32_t* __restrict__ Kp, uint32_t pnx, uint32_t pny,
+                                                  uint32_t bias, float3 t) {
+    const uint32_t bx = __float_as_uint(__fadd_rz(t.x, 8388608.0f));
+    const uint32_t by = __float_as_uint(__fadd_rz(t.y, 8388608.0f));
+    const uint32_t bz = __float_as_uint(__fadd_rz(t.z, 8388608.0f));
+    return __ldg(Kp + (bx + pnx * (by + pny * bz) - bias));
+}
+
+// Nearest-voxel value with the bounds test (shifted grid position t): the value
+// of the voxel (clamped to the box when outside) and whether t is inside.
+__device__ __forceinline__ uint32_t lookup_checked(const PocketDev& pd, const uint16_t* __restrict__ K, float3 t,
+                                                   bool* in) {
+    const uint32_t ix = vox(t.x), iy = vox(t.y), iz = vox(t.z);
+    *in = (ix < (uint32_t)pd.nx) & (iy < (uint32_t)pd.ny) & (iz < (uint32_t)pd.nz);
+    const int cx = min(max((int)ix, 0), pd.nx - 1), cy = min(max((int)iy, 0), pd.ny - 1),
+              cz = min(max((int)iz, 0), pd.nz - 1);
+    return __ldg(K + (cx + pd.nx * (cy + pd.ny * cz)));
+}
+
+// Squared distance outside the box of a shifted nearest-mode position.
+__device__ __forceinline__ float outside2(const PocketDev& pd, float3 t) {
+    const float ex = fmaxf(-t.x, 0.f) + fmaxf(t.x - (float)pd.nx, 0.f);
+    const float ey = fmaxf(-t.y, 0.f) + fmaxf(t.y - (float)pd.ny, 0.f);
+    const float ez = fmaxf(-t.z, 0.f) + fmaxf(t.z - (float)pd.nz, 0.f);
+    return ex * ex + ey * ey + ez * ez;
+}
+
+// Field terms of moving atoms at the chunk's KC angles, added to acc. The
+// angles' (cos, sin) come from the warp's shared table (the same for every
+// lane). fast: every circle lies inside the box, so no bounds tests. With
+// CLIP an angle that puts an atom outside sets its bit in box; without CLIP
+// the lookup is clamped and the squared distance outside goes to pen.
+template <int KC, int MODE, bool CLIP, int NA>
+__device__ __forceinline__ void score_atoms(const PocketDev& pd, const uint16_t* __restrict__ K, uint32_t bias,
+                                            const Split (&s)[NA], bool fast, const float2* __restrict__ cst,
+                                            typename Acc<MODE>::T (&acc)[KC], float (&pen)[KC], uint64_t& box) {
+    if (MODE == 0 && fast) {
+        // padded field: circle centres moved by PAD voxels; outside values sum past OUTSIDE
+        Split sp[NA];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            sp[a] = s[a];
+            sp[a].a = make_float3(s[a].a.x + (float)PAD, s[a].a.y + (float)PAD, s[a].a.z + (float)PAD);
+        }
+        const uint32_t pnx = (uint32_t)(pd.nx + 2 * PAD), pny = (uint32_t)(pd.ny + 2 * PAD);
 #pragma unroll
         for (int j = 0; j < KC; ++j) {
-            bool in;
-            acc[j] += term<MODE, CLIP>(pd, K, place(s, cj[j], sj[j]), &in);
-            if (CLIP && !in) box |= 1ull << j;
-        }
-        // bump pairs of this moving atom
-        float r2 = s.u.x * s.u.x + s.u.y * s.u.y + s.u.z * s.u.z;
-        float R = thr_g + sqrtf(r2) + 1e-3f;
-        float R2 = R * R;
-        for (int f = 0; f < nfixB; ++f) {
-            float3 y = ld3(xs, fixB[f], G, ps);
-            float dx = s.a.x - y.x, dy = s.a.y - y.y, dz = s.a.z - y.z;
-            float dd = dx * dx + dy * dy + dz * dz;
-            bool risk = live && dd < R2;
-            if (__any_sync(FULL, risk)) {
-                if (risk) {
-                    float A = dd + r2 - thr2;
-                    float B = 2.f * (dx * s.u.x + dy * s.u.y + dz * s.u.z);
-                    float C = 2.f * (dx * s.w.x + dy * s.w.y + dz * s.w.z);
+            const float2 c = cst[j];
 #pragma unroll
-                    for (int j = 0; j < KC; ++j)
-                        if (fmaf(sj[j], C, fmaf(cj[j], B, A)) < 0.f) bad |= 1ull << j;
+            for (int a = 0; a < NA; ++a) acc[j] += lookup_padded(pd.Kp, pnx, pny, bias, place(sp[a], c.x, c.y));
+        }
+    } else if (MODE == 0) {
+#pragma unroll
+        for (int j = 0; j < KC; ++j) {
+            const float2 c = cst[j];
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                const float3 t = place(s[a], c.x, c.y);
+                bool in;
+                acc[j] += lookup_checked(pd, K, t, &in);
+                if (!in) {
+                    if (CLIP) box |= 1ull << j;
+                    else pen[j] += outside2(pd, t);
                 }
             }
         }
-    }
-    unsigned long long best = ~0ull;
+    } else {
 #pragma unroll
-    for (int j = 0; j < KC; ++j) {
-        if (j < nvalid) {
-            float S = S_fix + acc[j];
-            bool clash = (bad >> j) & 1ull, out = (box >> j) & 1ull;
-            const int slot = slot_start + slot_step * j;
-            if (trace_S) {
-                trace_S[slot] = S;
-                trace_st[slot] = clash ? 0 : (out ? -1 : 1);
-            }
-            if (!clash && !out) {
-                unsigned long long key = make_key(S, slot);
-                best = key < best ? key : best;
+        for (int j = 0; j < KC; ++j) {
+            const float2 c = cst[j];
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                bool in;
+                acc[j] += term<1, CLIP>(pd, K, place(s[a], c.x, c.y), &in);
+                if (CLIP && !in) box |= 1ull << j;
             }
         }
     }
-    return best;
+}
+
+// Marks the candidates theta0 + j*dtheta (degrees, j < n) at which moving
+// atom x (split sp, in the candidates' frame) comes closer than thr to the
+// fixed atom y. d^2(theta) = A + B cos(theta) + C sin(theta) = A + R cos(theta - phi),
+// so the infeasible angles form one arc centred at phi + 180 of half-width
+// 180 - acos((thr^2 - A) / R) (degrees); its candidates get their bits set in
+// the lane's column col (stride 32 words).
+static __device__ __noinline__ void mark_arc(const Split& sp, float3 y, float thr2, float theta0, float dtheta, int n,
+                                             unsigned long long* col) {
+    const float dx = sp.a.x - y.x, dy = sp.a.y - y.y, dz = sp.a.z - y.z;
+    const float A = dx * dx + dy * dy + dz * dz + (sp.u.x * sp.u.x + sp.u.y * sp.u.y + sp.u.z * sp.u.z);
+    const float B = 2.f * (dx * sp.u.x + dy * sp.u.y + dz * sp.u.z);
+    const float C = 2.f * (dx * sp.w.x + dy * sp.w.y + dz * sp.w.z);
+    const float R = sqrtf(B * B + C * C);
+    float centre, half;
+    if (R <= 1e-12f * A) {
+        if (A >= thr2) return;  // distance does not change with the angle
+        centre = 180.f;
+        half = 360.f;
+    } else {
+        const float c = (thr2 - A) / R;
+        if (c <= -1.f) return;  // never closer than thr
+        const float deg = 57.29577951308232f;
+        centre = (atan2f(C, B) + 3.14159265358979f) * deg;  // in [0, 360]
+        half = c >= 1.f ? 360.f : 180.f - acosf(c) * deg;
+    }
+    for (int m = -1; m <= 1; ++m) {
+        const float lo = (centre - half + 360.f * m - theta0) / dtheta;
+        const float hi = (centre + half + 360.f * m - theta0) / dtheta;
+        // open interval (lo, hi): j from floor(lo) + 1 to ceil(hi) - 1
+        const int jl = max((int)floorf(lo) + 1, 0), jh = min((int)ceilf(hi) - 1, n - 1);
+        for (int j = jl; j <= jh;) {
+            const int w = j >> 6, b0 = j & 63, b1 = min(63, jh - (w << 6));
+            col[w * 32] |= (~0ull >> (63 - b1)) & (~0ull << b0);
+            j = (w + 1) << 6;
+        }
+    }
 }
 
 template <int KC, int MODE, bool CLIP>
-__global__ void __launch_bounds__(256) sweep_kernel(SweepParams P) {
+__global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParams P) {
     extern __shared__ float smem[];
+    using AT = typename Acc<MODE>::T;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int Q = P.Q;
-    const int G = 32 / Q;
-    const int ps = lane / Q;
-    const int q = lane % Q;
-    float* xs = smem + (size_t)warp * P.lmax * 3 * G;
+    float* xs = smem + (size_t)warp * (P.slice + warp_extra_floats(KC, P.bw));
+    unsigned long long* bump = reinterpret_cast<unsigned long long*>(xs + P.slice);  // [bw][32]
+    float2* cst = reinterpret_cast<float2*>(xs + P.slice + P.bw * 64);              // the chunk's (cos, sin)
+    unsigned long long* col = bump + lane;
     const float shift = MODE == 0 ? 0.5f : 0.0f;
 
     for (;;) {
@@ -333,13 +432,27 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepParams P) {
         task = __shfl_sync(FULL, task, 0);
         if (task >= P.ntask) break;
         const int2 tk = P.tasks[task];
+        const int lq = tk.y >> 16;
+        const int Q = 1 << lq;       // lanes per pose (they split the pose's atoms)
+        const int G = 32 >> lq;      // poses of this warp
+        const int ps = lane >> lq;   // pose slot
+        const int q = lane & (Q - 1);
         const int pocket = tk.x / P.nlig, b = tk.x % P.nlig;
         const PocketDev& pd = P.pockets[pocket];
         const uint16_t* __restrict__ K = pd.K;
+        const uint32_t pnx = (uint32_t)(pd.nx + 2 * PAD), pny = (uint32_t)(pd.ny + 2 * PAD);
+        const uint32_t bias = 0x4B000000u * (1u + pnx + pnx * pny);
         const LigDev L = P.lig[b];
-        const int p = tk.y * G + ps;
+        const int p = (tk.y & 0xffff) * G + ps;
         const bool active = p < P.n_poses;
         const float thr_g = (float)(P.bump_thr / pd.h);
+        const float thr2 = thr_g * thr_g;
+        const float nxf = (float)pd.nx, nyf = (float)pd.ny, nzf = (float)pd.nz;
+        // circle inside [lo, hi) per axis: no per-angle bounds test needed. With clipping
+        // the padded field flags outside positions by itself, so its padded box is enough.
+        const float lo = (MODE == 0 && CLIP) ? -(float)PAD : 0.f;
+        const float hix = MODE == 0 ? nxf - lo : nxf - 1.f, hiy = MODE == 0 ? nyf - lo : nyf - 1.f,
+                    hiz = MODE == 0 ? nzf - lo : nzf - 1.f;
 
         // ---- initial rigid orientation (FP64), centroid on the pocket centre
         {
@@ -358,18 +471,13 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepParams P) {
         __syncwarp();
         float S_inc = 0.f;
         bool inbox = true;
-        {
-            const int i0 = MODE == 0 ? q : 0, di = MODE == 0 ? Q : 1;
-            for (int i = i0; i < L.l; i += di) {
-                bool in;
-                S_inc += term<MODE, CLIP>(pd, K, ld3(xs, i, G, ps), &in);
-                inbox = inbox && in;
-            }
-            if (MODE == 0) {
-                S_inc = group_sum(S_inc, Q);
-                inbox = group_all(inbox, Q);
-            }
+        for (int i = q; i < L.l; i += Q) {
+            bool in;
+            S_inc += term<MODE, CLIP>(pd, K, ld3(xs, i, G, ps), &in);
+            inbox = inbox && in;
         }
+        S_inc = group_sum(S_inc, Q);
+        inbox = group_all(inbox, Q);
         const bool live = active && (!CLIP || inbox);
         const int nsweep = P.repetitions * L.nside;
         // trace layout: n_poses * repetitions * (sweeps of earlier ligands) + p * nsweep
@@ -394,6 +502,10 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepParams P) {
                     const int sweep = rep * L.nside + si;
                     const bool coarse = (double)sd.m / (double)L.l <= P.threshold;
                     const bool peel = P.peel && !coarse;
+                    const uint8_t* __restrict__ mov = P.idx + sd.mov_off;
+                    const uint8_t* __restrict__ fix = P.idx + sd.fix_off;  // F\{b}, then b, then c
+                    const int nmov = sd.nmov, nfixB = sd.nfixB;
+                    const int nslot = (nmov + Q - 1) / Q;  // moving atoms per lane (q + Q*s)
                     float* tS = nullptr;
                     int* tSt = nullptr;
                     if (P.trace_on && active) {
@@ -418,97 +530,212 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepParams P) {
                         kax.y *= inv;
                         kax.z *= inv;
                     }
-                    // fixed atoms' part of S (F plus the axis atom c). Nearest-mode terms
-                    // are integers, so splitting them over the pose's lanes is exact;
-                    // trilinear sums stay in one fixed order for every tile shape.
+                    // fixed atoms' part of S: F plus the axis atom c
                     float S_fix = 0.f;
-                    const uint8_t* fixS = P.idx + sd.fix_off;
-                    {
-                        const int i0 = MODE == 0 ? q : 0, di = MODE == 0 ? Q : 1;
-                        for (int i = i0; i < sd.nfixS; i += di) {
-                            bool in;
-                            S_fix += term<MODE, CLIP>(pd, K, ld3(xs, fixS[i], G, ps), &in);
-                        }
-                        if (MODE == 0) S_fix = group_sum(S_fix, Q);
+                    for (int i = q; i < sd.nfixS; i += Q) {
+                        bool in;
+                        S_fix += term<MODE, CLIP>(pd, K, ld3(xs, fix[i], G, ps), &in);
                     }
-                    const uint8_t* mov = P.idx + sd.mov_off;
-                    const uint8_t* fixB = P.idx + sd.fix_off;
+                    S_fix = group_sum(S_fix, Q);
 
                     unsigned long long best = make_key(S_inc, 0);
                     const float2* cs = coarse ? P.cs_lp : P.cs_hp;
-                    // candidate phases: flat sweep, or tile centres then the best tile
-                    int phases = peel ? 2 : 1;
-                    int tile_first = 0;  // first angle index of the best tile (hp table)
+                    const int phases = peel ? 2 : 1;
+                    int tile_first = 0;
                     bool have_tile = true;  // a pose with no feasible tile centre keeps its incumbent
+                    float2 pre = make_float2(1.f, 0.f);  // angle origin of this pose's candidates
                     for (int ph = 0; ph < phases; ++ph) {
+                        // candidates theta0 + j * dtheta (tab[j]), j < ncand, in trace slots slot0 + j
                         int ncand, slot0;
+                        float theta0, dtheta;
                         const float2* tab;
                         if (!peel) {
                             ncand = (coarse ? P.P_lp : P.P_hp) - 1;
                             tab = cs + 1;
                             slot0 = 1;
+                            theta0 = dtheta = coarse ? P.lp_step : P.hp_step;
                         } else if (ph == 0) {
                             ncand = P.n_tiles;
                             tab = P.cs_peel;
                             slot0 = 1;
+                            theta0 = 0.5f * P.tile;
+                            dtheta = P.tile;
                         } else {
+                            // the tile's angles relative to its start, the same for every pose;
+                            // each pose turns its circles to its own tile start (pre)
                             ncand = P.per_tile;
-                            tab = P.cs_hp + tile_first;
+                            tab = P.cs_hp;
                             slot0 = 1 + P.n_tiles;
+                            theta0 = 0.f;
+                            dtheta = P.hp_step;
                         }
+
+                        // ---- bump check for the whole phase. The closest approach of fixed atom y
+                        // to the circle of moving atom x is sqrt((rho_y - r_x)^2 + (h_y - h_x)^2)
+                        // (rho: distance from the axis, h: position along it); pairs that come within
+                        // the threshold get the arc of angles where they do marked.
+                        const int nw = (ncand + 63) >> 6;
+                        for (int w = 0; w < nw; ++w) col[w * 32] = 0ull;
+                        {
+                            const float lim = thr2 + 0.05f;  // margin over the FP32 error of the bound
+                            for (int s0 = 0; s0 < nslot; s0 += 8) {
+                                float r[8], h[8];
+#pragma unroll
+                                for (int j = 0; j < 8; ++j) {
+                                    const int im = q + Q * (s0 + j);
+                                    r[j] = 1e18f;  // no atom: never close (its square stays finite)
+                                    h[j] = 0.f;
+                                    if (s0 + j < nslot && im < nmov) {
+                                        float3 x = ld3(xs, mov[im], G, ps);
+                                        float vx = x.x - gc.x, vy = x.y - gc.y, vz = x.z - gc.z;
+                                        float t = kax.x * vx + kax.y * vy + kax.z * vz;
+                                        r[j] = sqrtf(fmaxf(vx * vx + vy * vy + vz * vz - t * t, 0.f));
+                                        h[j] = t;
+                                    }
+                                }
+                                for (int f = 0; f < nfixB; ++f) {
+                                    const float3 y = ld3(xs, fix[f], G, ps);
+                                    const float wx = y.x - gc.x, wy = y.y - gc.y, wz = y.z - gc.z;
+                                    const float t = kax.x * wx + kax.y * wy + kax.z * wz;
+                                    const float rho = sqrtf(fmaxf(wx * wx + wy * wy + wz * wz - t * t, 0.f));
+                                    unsigned near = 0;
+#pragma unroll
+                                    for (int j = 0; j < 8; ++j) {
+                                        const float dr = rho - r[j], dh = t - h[j];
+                                        if (fmaf(dr, dr, dh * dh) < lim) near |= 1u << j;
+                                    }
+                                    if (!live || !have_tile) near = 0;
+                                    while (near) {
+                                        const int j = __ffs(near) - 1;
+                                        near &= near - 1;
+                                        const Split sp =
+                                            turn(split(ld3(xs, mov[q + Q * (s0 + j)], G, ps), gc, kax), pre);
+                                        mark_arc(sp, y, thr2, theta0, dtheta, ncand, col);
+                                    }
+                                }
+                            }
+                        }
+
                         unsigned long long pbest = ~0ull;
-                        // lane q takes candidates q, q+Q, q+2Q, ...
-                        const int per_lane = (ncand + Q - 1) / Q;
-                        for (int j0 = 0; j0 < per_lane; j0 += KC) {
-                            float2 csj[KC];
-                            int nvalid = 0;
+                        for (int j0 = 0; j0 < ncand; j0 += KC) {
+                            // the chunk's angles are the same for every lane of the warp
+                            const int nvalid = min(KC, ncand - j0);
+                            __syncwarp();
+                            for (int j = lane; j < KC; j += 32) cst[j] = j < nvalid ? tab[j0 + j] : make_float2(1.f, 0.f);
+                            __syncwarp();
+                            AT acc[KC];
+                            float pen[KC];
 #pragma unroll
                             for (int j = 0; j < KC; ++j) {
-                                int c = q + Q * (j0 + j);
-                                bool ok = (j0 + j) < per_lane && c < ncand && have_tile;
-                                const float2 v = tab[ok ? c : 0];  // index 0 is always in the table
-                                csj[j] = ok ? v : make_float2(1.f, 0.f);
-                                nvalid += ok ? 1 : 0;
+                                acc[j] = (AT)0;
+                                pen[j] = 0.f;
                             }
-                            // valid candidates of a lane are a prefix of its chunk
-                            unsigned long long cb = sweep_chunk<KC, MODE, CLIP>(
-                                pd, K, xs, G, ps, mov, sd.nmov, fixB, sd.nfixB, gc, kax, thr_g, S_fix,
-                                live && have_tile, csj, slot0 + q + Q * j0, Q, nvalid, tS, tSt);
-                            pbest = cb < pbest ? cb : pbest;
+                            uint64_t box = 0ull;
+                            auto circle_inside = [&](const Split& sp) {
+                                const float rad = sqrtf(sp.u.x * sp.u.x + sp.u.y * sp.u.y + sp.u.z * sp.u.z) + 1e-3f;
+                                return sp.a.x - rad >= lo && sp.a.x + rad < hix && sp.a.y - rad >= lo &&
+                                       sp.a.y + rad < hiy && sp.a.z - rad >= lo && sp.a.z + rad < hiz;
+                            };
+                            // two moving atoms per pass share each angle's table load (small chunks)
+                            int s = 0;
+                            for (; KC <= 18 && s + 1 < nslot; s += 2) {
+                                const int i0 = q + Q * s, i1 = i0 + Q;
+                                const bool h1 = i1 < nmov;  // i0 < nmov whenever s + 1 < nslot
+                                Split sp[2];
+                                sp[0] = turn(split(ld3(xs, mov[i0], G, ps), gc, kax), pre);
+                                sp[1] = turn(split(ld3(xs, mov[h1 ? i1 : i0], G, ps), gc, kax), pre);
+                                const bool fast = __all_sync(FULL, circle_inside(sp[0]) && (circle_inside(sp[1]) || !h1));
+                                if (h1) {
+                                    score_atoms<KC, MODE, CLIP, 2>(pd, K, bias, sp, fast, cst, acc, pen, box);
+                                } else {
+                                    Split one[1] = {sp[0]};
+                                    score_atoms<KC, MODE, CLIP, 1>(pd, K, bias, one, fast, cst, acc, pen, box);
+                                }
+                            }
+                            for (; s < nslot; ++s) {
+                                const int i0 = q + Q * s;
+                                const bool h0 = i0 < nmov;
+                                Split one[1] = {turn(split(ld3(xs, mov[h0 ? i0 : 0], G, ps), gc, kax), pre)};
+                                const bool fast = __all_sync(FULL, circle_inside(one[0]) || !h0);
+                                if (h0) score_atoms<KC, MODE, CLIP, 1>(pd, K, bias, one, fast, cst, acc, pen, box);
+                            }
+                            // this chunk's bump bits
+                            uint64_t bad;
+                            {
+                                const int w = j0 >> 6, sh = j0 & 63;
+                                bad = col[w * 32] >> sh;
+                                if (sh + KC > 64 && w + 1 < P.bw) bad |= col[(w + 1) * 32] << (64 - sh);
+                            }
+                            // combine the pose's lanes: every lane then holds the pose's full values
+                            bad = group_or(bad, Q);
+                            if (CLIP) box = group_or(box, Q);
+#pragma unroll
+                            for (int j = 0; j < KC; ++j) {
+                                if (MODE == 0) acc[j] = (AT)group_add_u((uint32_t)acc[j], Q);
+                                else acc[j] = (AT)group_sum((float)acc[j], Q);
+                                if (!CLIP) pen[j] = group_sum(pen[j], Q);
+                            }
+#pragma unroll
+                            for (int j = 0; j < KC; ++j) {
+                                const float S = S_fix + (float)acc[j] + (CLIP ? 0.f : pen[j]);
+                                const bool ok = j < nvalid && have_tile && !((bad >> j) & 1ull) &&
+                                                !(CLIP && (((box >> j) & 1ull) || (MODE == 0 && (uint32_t)acc[j] >= OUTSIDE)));
+                                const unsigned long long key = make_key(S, slot0 + j0 + j);
+                                pbest = (ok && key < pbest) ? key : pbest;
+                            }
+                            if (tS && q == 0) {
+                                // trace: every evaluated candidate's S and status
+#pragma unroll 1
+                                for (int j = 0; j < nvalid; ++j) {
+                                    if (!have_tile) break;
+                                    float accj = 0.f, penj = 0.f;
+                                    bool outj = false;
+#pragma unroll
+                                    for (int i = 0; i < KC; ++i)
+                                        if (i == j) {
+                                            accj = (float)acc[i];
+                                            penj = CLIP ? 0.f : pen[i];
+                                            outj = MODE == 0 && (uint32_t)acc[i] >= OUTSIDE;
+                                        }
+                                    const bool clash = (bad >> j) & 1ull;
+                                    const bool out = CLIP && (((box >> j) & 1ull) || outj);
+                                    tS[slot0 + j0 + j] = S_fix + accj + penj;
+                                    tSt[slot0 + j0 + j] = clash ? 0 : (out ? -1 : 1);
+                                }
+                            }
                         }
-                        pbest = group_min(pbest, Q);
                         if (peel && ph == 0) {
-                            // the best tile centre picks the tile; the tile's angles are the next phase
+                            // the best tile centre picks the tile; its angles are the next phase
                             have_tile = pbest != ~0ull;
-                            int t = have_tile ? (int)(pbest & 0xffffffffu) - 1 : 0;
+                            const int t = have_tile ? (int)(pbest & 0xffffffffu) - 1 : 0;
                             tile_first = t * P.per_tile;
+                            pre = P.cs_hp[tile_first];
                         } else {
                             best = pbest < best ? pbest : best;
                         }
                     }
-                    best = group_min(best, Q);
-                    const int kb = (int)(best & 0xffffffffu);
-                    if (live && kb != 0) {
-                        float2 v;
-                        if (!peel) v = cs[kb];
-                        else v = P.cs_hp[tile_first + (kb - 1 - P.n_tiles)];
-                        if (q == 0) {
-                            for (int im = 0; im < sd.nmov; ++im) {
+                    const int kb = live ? (int)(best & 0xffffffffu) : 0;
+                    if (kb != 0) {
+                        // the same rotation as the candidate's evaluation
+                        const float2 v = !peel ? cs[kb] : P.cs_hp[kb - 1 - P.n_tiles];
+                        const float2 r0 = !peel ? make_float2(1.f, 0.f) : pre;
+                        for (int s = 0; s < nslot; ++s) {
+                            const int im = q + Q * s;
+                            if (im < nmov) {
                                 const int i = mov[im];
-                                Split s = split(ld3(xs, i, G, ps), gc, kax);
-                                st3(xs, i, G, ps, place(s, v.x, v.y));
+                                st3(xs, i, G, ps, place(turn(split(ld3(xs, i, G, ps), gc, kax), r0), v.x, v.y));
                             }
                         }
                         S_inc = __uint_as_float((unsigned)(best >> 32));
                     }
-                    if (P.trace_on && active && q == 0) P.tr.chosen_k[tbase + sweep] = live ? kb : 0;
+                    if (P.trace_on && active && q == 0) P.tr.chosen_k[tbase + sweep] = kb;
                     __syncwarp();
                 }
             }
         }
         // ---- per-pose result
         if (active && q == 0) {
-            int64_t pi = (int64_t)tk.x * P.n_poses + p;
+            const int64_t pi = (int64_t)tk.x * P.n_poses + p;
             P.pose_key[pi] = live ? make_key(S_inc, p) : ~0ull;
             float* o = P.pose_xyz + ((int64_t)pocket * P.natoms * P.n_poses + (int64_t)L.atom_off * P.n_poses +
                                      (int64_t)p * L.l) * 3;
@@ -519,7 +746,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepParams P) {
                 o[3 * i + 2] = t.z;
             }
             if (P.trace_on) {
-                int64_t ti = (int64_t)b * P.n_poses + p;
+                const int64_t ti = (int64_t)b * P.n_poses + p;
                 P.tr.pose_S[ti] = live ? S_inc : 0.f;
                 for (int i = 0; i < L.l; ++i) {
                     float3 t = ld3(xs, i, G, ps);
@@ -553,7 +780,7 @@ struct FinalParams {
 
 // One warp per (pocket, ligand): best pose over the initial poses (lowest S,
 // ties to the lowest pose), its coordinates back to Å.
-__global__ void finalize_kernel(FinalParams F) {
+static __global__ void finalize_kernel(FinalParams F) {
     const int lane = threadIdx.x & 31;
     const int pair = F.pair0 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (pair >= F.pair0 + F.npairs) return;
@@ -595,7 +822,7 @@ __global__ void finalize_kernel(FinalParams F) {
 
 // K(v) = max(min_j |v - p_j|^2, 1), exact integers; one thread per voxel,
 // probe points staged through shared memory.
-__global__ void field_kernel(uint16_t* K, int nx, int ny, int nz, const int4* pts, int npts) {
+static __global__ void field_kernel(uint16_t* K, int nx, int ny, int nz, const int4* pts, int npts) {
     __shared__ int4 sp[256];
     const int64_t nvox = (int64_t)nx * ny * nz;
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -617,6 +844,16 @@ __global__ void field_kernel(uint16_t* K, int nx, int ny, int nz, const int4* pt
         }
     }
     if (v < nvox) K[v] = (uint16_t)max(best, 1);
+}
+// Padded copy of the field: PAD voxels of OUTSIDE around the grid.
+static __global__ void pad_field_kernel(uint32_t* Kp, const uint16_t* K, int nx, int ny, int nz) {
+    const int pnx = nx + 2 * PAD, pny = ny + 2 * PAD, pnz = nz + 2 * PAD;
+    const int64_t n = (int64_t)pnx * pny * pnz;
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int x = (int)(v % pnx) - PAD, y = (int)((v / pnx) % pny) - PAD, z = (int)(v / ((int64_t)pnx * pny)) - PAD;
+    const bool in = x >= 0 && y >= 0 && z >= 0 && x < nx && y < ny && z < nz;
+    Kp[v] = in ? (uint32_t)K[(int64_t)z * ny * nx + (int64_t)y * nx + x] : OUTSIDE;
 }
 #endif  // GD_DEFINE_AUX_KERNELS
 
