@@ -268,9 +268,14 @@ __device__ __forceinline__ unsigned long long make_key(float S, int k) {
 // run uses bw = ceil(largest phase / 64) of them.
 constexpr int BW = 7;
 // Besides its coordinate slice a warp keeps in shared memory only the bump
-// bits (bw words per lane) and the chunk's angles: the rest of the SM's
-// shared memory serves as L1 cache for the field lookups.
-__host__ __device__ constexpr int warp_extra_floats(int kc, int bw) { return bw * 64 + 2 * kc; }
+// bits (bw words per lane), the phase's candidate angles (64 bw, plus a
+// chunk's worth of padding) and the sweep's atom-index lists (up to 258
+// bytes): the rest of the SM's shared memory serves as L1 cache for the field
+// lookups.
+constexpr int IDX_FLOATS = 68;
+__host__ __device__ constexpr int warp_extra_floats(int kc, int bw) {
+    return bw * 64 + 2 * (64 * bw + kc) + IDX_FLOATS;
+}
 
 // 32-bit sums over the Q lanes of a pose.
 __device__ __forceinline__ uint32_t group_add_u(uint32_t v, int Q) {
@@ -376,44 +381,6 @@ __device__ __forceinline__ void score_atoms(const PocketDev& pd, const uint16_t*
     }
 }
 
-// Marks the candidates theta0 + j*dtheta (degrees, j < n) at which moving
-// atom x (split sp, in the candidates' frame) comes closer than thr to the
-// fixed atom y. d^2(theta) = A + B cos(theta) + C sin(theta) = A + R cos(theta - phi),
-// so the infeasible angles form one arc centred at phi + 180 of half-width
-// 180 - acos((thr^2 - A) / R) (degrees); its candidates get their bits set in
-// the lane's column col (stride 32 words).
-static __device__ __noinline__ void mark_arc(const Split& sp, float3 y, float thr2, float theta0, float dtheta, int n,
-                                             unsigned long long* col) {
-    const float dx = sp.a.x - y.x, dy = sp.a.y - y.y, dz = sp.a.z - y.z;
-    const float A = dx * dx + dy * dy + dz * dz + (sp.u.x * sp.u.x + sp.u.y * sp.u.y + sp.u.z * sp.u.z);
-    const float B = 2.f * (dx * sp.u.x + dy * sp.u.y + dz * sp.u.z);
-    const float C = 2.f * (dx * sp.w.x + dy * sp.w.y + dz * sp.w.z);
-    const float R = sqrtf(B * B + C * C);
-    float centre, half;
-    if (R <= 1e-12f * A) {
-        if (A >= thr2) return;  // distance does not change with the angle
-        centre = 180.f;
-        half = 360.f;
-    } else {
-        const float c = (thr2 - A) / R;
-        if (c <= -1.f) return;  // never closer than thr
-        const float deg = 57.29577951308232f;
-        centre = (atan2f(C, B) + 3.14159265358979f) * deg;  // in [0, 360]
-        half = c >= 1.f ? 360.f : 180.f - acosf(c) * deg;
-    }
-    for (int m = -1; m <= 1; ++m) {
-        const float lo = (centre - half + 360.f * m - theta0) / dtheta;
-        const float hi = (centre + half + 360.f * m - theta0) / dtheta;
-        // open interval (lo, hi): j from floor(lo) + 1 to ceil(hi) - 1
-        const int jl = max((int)floorf(lo) + 1, 0), jh = min((int)ceilf(hi) - 1, n - 1);
-        for (int j = jl; j <= jh;) {
-            const int w = j >> 6, b0 = j & 63, b1 = min(63, jh - (w << 6));
-            col[w * 32] |= (~0ull >> (63 - b1)) & (~0ull << b0);
-            j = (w + 1) << 6;
-        }
-    }
-}
-
 template <int KC, int MODE, bool CLIP>
 __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParams P) {
     extern __shared__ float smem[];
@@ -422,7 +389,8 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
     const int warp = threadIdx.x >> 5;
     float* xs = smem + (size_t)warp * (P.slice + warp_extra_floats(KC, P.bw));
     unsigned long long* bump = reinterpret_cast<unsigned long long*>(xs + P.slice);  // [bw][32]
-    float2* cst = reinterpret_cast<float2*>(xs + P.slice + P.bw * 64);              // the chunk's (cos, sin)
+    float2* ptab = reinterpret_cast<float2*>(xs + P.slice + P.bw * 64);             // the phase's (cos, sin)
+    uint8_t* sidx = reinterpret_cast<uint8_t*>(ptab + 64 * P.bw + KC);              // the sweep's index lists
     unsigned long long* col = bump + lane;
     const float shift = MODE == 0 ? 0.5f : 0.0f;
 
@@ -502,8 +470,13 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                     const int sweep = rep * L.nside + si;
                     const bool coarse = (double)sd.m / (double)L.l <= P.threshold;
                     const bool peel = P.peel && !coarse;
-                    const uint8_t* __restrict__ mov = P.idx + sd.mov_off;
-                    const uint8_t* __restrict__ fix = P.idx + sd.fix_off;  // F\{b}, then b, then c
+                    // the sweep's index lists, staged in shared memory: M\{c}, then F\{b}, b, c
+                    __syncwarp();
+                    for (int i = lane; i < sd.nmov + sd.nfixS; i += 32)
+                        sidx[i] = P.idx[i < sd.nmov ? sd.mov_off + i : sd.fix_off + (i - sd.nmov)];
+                    __syncwarp();
+                    const uint8_t* mov = sidx;
+                    const uint8_t* fix = sidx + sd.nmov;
                     const int nmov = sd.nmov, nfixB = sd.nfixB;
                     const int nslot = (nmov + Q - 1) / Q;  // moving atoms per lane (q + Q*s)
                     float* tS = nullptr;
@@ -545,29 +518,23 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                     bool have_tile = true;  // a pose with no feasible tile centre keeps its incumbent
                     float2 pre = make_float2(1.f, 0.f);  // angle origin of this pose's candidates
                     for (int ph = 0; ph < phases; ++ph) {
-                        // candidates theta0 + j * dtheta (tab[j]), j < ncand, in trace slots slot0 + j
+                        // candidates tab[j], j < ncand, in trace slots slot0 + j
                         int ncand, slot0;
-                        float theta0, dtheta;
                         const float2* tab;
                         if (!peel) {
                             ncand = (coarse ? P.P_lp : P.P_hp) - 1;
                             tab = cs + 1;
                             slot0 = 1;
-                            theta0 = dtheta = coarse ? P.lp_step : P.hp_step;
                         } else if (ph == 0) {
                             ncand = P.n_tiles;
                             tab = P.cs_peel;
                             slot0 = 1;
-                            theta0 = 0.5f * P.tile;
-                            dtheta = P.tile;
                         } else {
                             // the tile's angles relative to its start, the same for every pose;
                             // each pose turns its circles to its own tile start (pre)
                             ncand = P.per_tile;
                             tab = P.cs_hp;
                             slot0 = 1 + P.n_tiles;
-                            theta0 = 0.f;
-                            dtheta = P.hp_step;
                         }
 
                         // ---- bump check for the whole phase. The closest approach of fixed atom y
@@ -576,6 +543,10 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                         // the threshold get the arc of angles where they do marked.
                         const int nw = (ncand + 63) >> 6;
                         for (int w = 0; w < nw; ++w) col[w * 32] = 0ull;
+                        // the phase's angles, the same for every lane; (1, 0) past the end
+                        __syncwarp();
+                        for (int j = lane; j < 64 * P.bw + KC; j += 32) ptab[j] = j < ncand ? tab[j] : make_float2(1.f, 0.f);
+                        __syncwarp();
                         {
                             const float lim = thr2 + 0.05f;  // margin over the FP32 error of the bound
                             for (int s0 = 0; s0 < nslot; s0 += 8) {
@@ -593,24 +564,57 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                                         h[j] = t;
                                     }
                                 }
-                                for (int f = 0; f < nfixB; ++f) {
-                                    const float3 y = ld3(xs, fix[f], G, ps);
-                                    const float wx = y.x - gc.x, wy = y.y - gc.y, wz = y.z - gc.z;
-                                    const float t = kax.x * wx + kax.y * wy + kax.z * wz;
-                                    const float rho = sqrtf(fmaxf(wx * wx + wy * wy + wz * wz - t * t, 0.f));
-                                    unsigned near = 0;
+                                // fixed atoms two at a time (independent loads in flight)
+                                for (int f = 0; f < nfixB; f += 2) {
+                                    const int f1 = f + 1 < nfixB ? f + 1 : f;
+                                    const float3 y0 = ld3(xs, fix[f], G, ps), y1 = ld3(xs, fix[f1], G, ps);
+                                    unsigned near0 = 0, near1 = 0;
+                                    {
+                                        const float wx = y0.x - gc.x, wy = y0.y - gc.y, wz = y0.z - gc.z;
+                                        const float t0 = kax.x * wx + kax.y * wy + kax.z * wz;
+                                        const float rho0 = sqrtf(fmaxf(wx * wx + wy * wy + wz * wz - t0 * t0, 0.f));
+                                        const float vx = y1.x - gc.x, vy = y1.y - gc.y, vz = y1.z - gc.z;
+                                        const float t1 = kax.x * vx + kax.y * vy + kax.z * vz;
+                                        const float rho1 = sqrtf(fmaxf(vx * vx + vy * vy + vz * vz - t1 * t1, 0.f));
 #pragma unroll
-                                    for (int j = 0; j < 8; ++j) {
-                                        const float dr = rho - r[j], dh = t - h[j];
-                                        if (fmaf(dr, dr, dh * dh) < lim) near |= 1u << j;
+                                        for (int j = 0; j < 8; ++j) {
+                                            const float dr0 = rho0 - r[j], dh0 = t0 - h[j];
+                                            const float dr1 = rho1 - r[j], dh1 = t1 - h[j];
+                                            if (fmaf(dr0, dr0, dh0 * dh0) < lim) near0 |= 1u << j;
+                                            if (fmaf(dr1, dr1, dh1 * dh1) < lim) near1 |= 1u << j;
+                                        }
                                     }
-                                    if (!live || !have_tile) near = 0;
-                                    while (near) {
-                                        const int j = __ffs(near) - 1;
-                                        near &= near - 1;
+                                    if (!live || !have_tile) near0 = 0;
+                                    if (!live || !have_tile || f1 == f) near1 = 0;
+                                    unsigned long long pairs = near0 | ((unsigned long long)near1 << 8);
+                                    while (pairs) {
+                                        const int e = __ffsll(pairs) - 1;
+                                        pairs &= pairs - 1;
+                                        const float3 y = e < 8 ? y0 : y1;
                                         const Split sp =
-                                            turn(split(ld3(xs, mov[q + Q * (s0 + j)], G, ps), gc, kax), pre);
-                                        mark_arc(sp, y, thr2, theta0, dtheta, ncand, col);
+                                            turn(split(ld3(xs, mov[q + Q * (s0 + (e & 7))], G, ps), gc, kax), pre);
+                                        // d^2(theta) = A + B cos(theta) + C sin(theta) at every candidate
+                                        const float dx = sp.a.x - y.x, dy = sp.a.y - y.y, dz = sp.a.z - y.z;
+                                        const float A = dx * dx + dy * dy + dz * dz +
+                                                        (sp.u.x * sp.u.x + sp.u.y * sp.u.y + sp.u.z * sp.u.z);
+                                        const float B = 2.f * (dx * sp.u.x + dy * sp.u.y + dz * sp.u.z);
+                                        const float C = 2.f * (dx * sp.w.x + dy * sp.w.y + dz * sp.w.z);
+                                        for (int w = 0; w < nw; ++w) {
+                                            const float4* tw = reinterpret_cast<const float4*>(ptab + 64 * w);
+                                            const int gend = min(64, ncand - 64 * w);
+                                            unsigned long long m = 0;
+                                            for (int g = 0; g < gend; g += 16) {
+                                                unsigned m16 = 0;
+#pragma unroll
+                                                for (int k = 0; k < 8; ++k) {
+                                                    const float4 t = tw[(g >> 1) + k];
+                                                    if (fmaf(C, t.y, fmaf(B, t.x, A)) < thr2) m16 |= 1u << (2 * k);
+                                                    if (fmaf(C, t.w, fmaf(B, t.z, A)) < thr2) m16 |= 2u << (2 * k);
+                                                }
+                                                m |= (unsigned long long)m16 << g;
+                                            }
+                                            col[w * 32] |= m;
+                                        }
                                     }
                                 }
                             }
@@ -620,9 +624,7 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                         for (int j0 = 0; j0 < ncand; j0 += KC) {
                             // the chunk's angles are the same for every lane of the warp
                             const int nvalid = min(KC, ncand - j0);
-                            __syncwarp();
-                            for (int j = lane; j < KC; j += 32) cst[j] = j < nvalid ? tab[j0 + j] : make_float2(1.f, 0.f);
-                            __syncwarp();
+                            const float2* cst = ptab + j0;
                             AT acc[KC];
                             float pen[KC];
 #pragma unroll
