@@ -31,6 +31,19 @@ UNIT = "ligands/s"
 WORKLOAD = "batched: 1024 ligands (16-64 atoms, 2-12 rotatable bonds) x 1 pocket 64^3 @0.5A, 64 poses, 10 deg, 4 reps"
 
 
+# DRAM bytes (read + write) of one sweep launch on this workload, from ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum), valid for the kernel source
+# with this sha256 prefix only; reported as null for any other source.
+NCU_TRAFFIC = {"kernel_sha256": "2c720043d49dac45", "bytes": 2799360 + 1024}
+
+
+def _traffic():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_1901_06363_gb300", "csrc", "geodock_kernels.cuh"), "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    return NCU_TRAFFIC["bytes"] if sha == NCU_TRAFFIC["kernel_sha256"] else None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -266,7 +279,7 @@ def run_ours(args):
         "plain_ligands_per_s": world * n / plain_s,
         "batched_vs_plain": (value / world) / (n / plain_s),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_inst, "unit": "Tinst/s",
-                     "frac": achieved / peak_inst, "traffic": None,
+                     "frac": achieved / peak_inst, "traffic": _traffic(), "traffic_unit": "bytes per launch (ncu)",
                      "kernel": "sweep_kernel", "sweep_ms": sweep_avg,
                      "peak_source": f"152 SMs x 128 lanes x sm_max_mhz {f_mhz:.0f} ({src} clocks)"},
         "cpu_baseline": cpu_baseline(pk, batch, kn) if world == 1 else None,
