@@ -67,6 +67,27 @@ class Out(ctypes.Structure):
                 ("cand_status", P(ctypes.c_int32)), ("cand_amb", P(ctypes.c_int32))]
 
 
+class RefineKnobs(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("clip_box", ctypes.c_int), ("bump_thr", ctypes.c_double),
+                ("lambda0", ctypes.c_double), ("lambda_max", ctypes.c_double), ("grow", ctypes.c_double),
+                ("shrink", ctypes.c_double), ("amb_delta", ctypes.c_double), ("amb_bump", ctypes.c_double),
+                ("amb_rel", ctypes.c_double)]
+
+
+class RefineOut(ctypes.Structure):
+    _fields_ = [("S_start", P(ctypes.c_double)), ("S_final", P(ctypes.c_double)), ("status", P(ctypes.c_int32)),
+                ("xyz", P(ctypes.c_double)), ("gstride", ctypes.c_int32), ("G", P(ctypes.c_double)),
+                ("D", P(ctypes.c_double)), ("lam", P(ctypes.c_double)), ("S_new", P(ctypes.c_double)),
+                ("verdict", P(ctypes.c_int32)), ("accept", P(ctypes.c_int32)), ("flags", P(ctypes.c_int32)),
+                ("force_accept", P(ctypes.c_int32))]
+
+
+# Step-length rule of the local refinement (largest atom displacement, Å):
+# start at LAMBDA0, times GROW after an accepted step (at most LAMBDA_MAX),
+# times SHRINK after a rejected one.
+LAMBDA0, LAMBDA_MAX, GROW, SHRINK = 0.25, 1.0, 1.5, 0.5
+
+
 def _load():
     global _lib
     with _lock:
@@ -91,6 +112,18 @@ def _load():
             lib.oracle_pose_rotation.restype = None
             lib.oracle_dock.argtypes = [P(Grid), P(Ligands), P(Knobs), P(Out), ctypes.c_int]
             lib.oracle_dock.restype = ctypes.c_int
+            D, I32 = P(ctypes.c_double), P(ctypes.c_int32)
+            lib.oracle_trilinear_grad.argtypes = [P(Grid), ctypes.c_int, D, ctypes.c_int, D, D, P(ctypes.c_int)]
+            lib.oracle_trilinear_grad.restype = ctypes.c_int
+            lib.oracle_torsions.argtypes = [P(Ligands), ctypes.c_int, I32, I32, I32, P(ctypes.c_uint8), I32,
+                                            P(ctypes.c_uint8)]
+            lib.oracle_torsions.restype = ctypes.c_int
+            lib.oracle_dof_apply.argtypes = [P(Ligands), ctypes.c_int, D, D, D]
+            lib.oracle_dof_apply.restype = ctypes.c_int
+            lib.oracle_dof_grad.argtypes = [P(Ligands), ctypes.c_int, D, D, D, D]
+            lib.oracle_dof_grad.restype = ctypes.c_int
+            lib.oracle_refine.argtypes = [P(Grid), P(Ligands), P(RefineKnobs), D, P(RefineOut), ctypes.c_int]
+            lib.oracle_refine.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -197,6 +230,23 @@ def sweep_layout(batch, kn):
     return nsw, base, int((nsw * kn["n_poses"]).sum())
 
 
+def _ligands(batch, ids=None, keep=None):
+    L = Ligands()
+    L.n = batch.n
+    L.atom_off = _ptr(batch.atom_off, ctypes.c_int32)
+    L.xyz = _ptr(batch.xyz, ctypes.c_float)
+    L.bond_off = _ptr(batch.bond_off, ctypes.c_int32)
+    L.bonds = _ptr(batch.bonds, ctypes.c_int32)
+    L.rot_off = _ptr(batch.rot_off, ctypes.c_int32)
+    L.rot = _ptr(batch.rot, ctypes.c_int32)
+    L.id_base = batch.id_base
+    if ids is not None:
+        ids = np.ascontiguousarray(ids, np.int64)
+        keep.append(ids)
+        L.ids = _ptr(ids, ctypes.c_int64)
+    return L
+
+
 def dock(opk: OraclePocket, batch, kn, trace=False, force_k=None, amb_delta=0.0, amb_bump=0.0, nthreads=None,
          xyz_out=False, ids=None):
     """Run the greedy sweep of Alg. 2 for every (ligand, initial pose); returns a dict of arrays.
@@ -243,19 +293,7 @@ def dock(opk: OraclePocket, batch, kn, trace=False, force_k=None, amb_delta=0.0,
             keep.append(fk)
             o.force_k = _ptr(fk, ctypes.c_int32)
     g = opk.cstruct()
-    L = Ligands()
-    L.n = n
-    L.atom_off = _ptr(batch.atom_off, ctypes.c_int32)
-    L.xyz = _ptr(batch.xyz, ctypes.c_float)
-    L.bond_off = _ptr(batch.bond_off, ctypes.c_int32)
-    L.bonds = _ptr(batch.bonds, ctypes.c_int32)
-    L.rot_off = _ptr(batch.rot_off, ctypes.c_int32)
-    L.rot = _ptr(batch.rot, ctypes.c_int32)
-    L.id_base = batch.id_base
-    if ids is not None:
-        ids = np.ascontiguousarray(ids, np.int64)
-        keep.append(ids)
-        L.ids = _ptr(ids, ctypes.c_int64)
+    L = _ligands(batch, ids, keep)
     k = Knobs()
     k.hp_step, k.lp_step, k.threshold = float(kn["hp_step"]), float(kn["lp_step"]), float(kn["threshold"])
     k.repetitions, k.n_poses, k.clip_box = int(kn["repetitions"]), N, int(kn["clip_box"])
@@ -268,4 +306,101 @@ def dock(opk: OraclePocket, batch, kn, trace=False, force_k=None, amb_delta=0.0,
     if rc != 0:
         raise ValueError(f"oracle_dock: bad knobs ({rc})")
     res["threads"] = int(nthreads)
+    return res
+
+
+# ---------------------------------------------------------------- local refinement (not in the paper)
+
+def trilinear_grad(opk: OraclePocket, xyz, clip=1):
+    """Trilinear S (grid units), dS/dx (grid units per Å, shape (l, 3)) and the inside flag."""
+    x = np.ascontiguousarray(xyz, np.float64).reshape(-1, 3)
+    dS = np.zeros_like(x)
+    S = ctypes.c_double(0)
+    inside = ctypes.c_int(0)
+    g = opk.cstruct()
+    _load().oracle_trilinear_grad(ctypes.byref(g), int(clip), _ptr(x, ctypes.c_double), len(x), ctypes.byref(S),
+                                  _ptr(dS, ctypes.c_double), ctypes.byref(inside))
+    return S.value, dS, bool(inside.value)
+
+
+def torsions(batch, b):
+    """Torsion layout of ligand b: dict of c, b, depth, mask (T, l), order (application), check (l, l)."""
+    l = int(batch.atom_off[b + 1] - batch.atom_off[b])
+    T = int(batch.rot_off[b + 1] - batch.rot_off[b])
+    c, bb, depth, order = (np.zeros(max(T, 1), np.int32) for _ in range(4))
+    mask = np.zeros(max(T, 1) * l, np.uint8)
+    check = np.zeros(l * l, np.uint8)
+    keep = []
+    L = _ligands(batch, None, keep)
+    r = _load().oracle_torsions(ctypes.byref(L), int(b), _ptr(c, ctypes.c_int32), _ptr(bb, ctypes.c_int32),
+                                _ptr(depth, ctypes.c_int32), _ptr(mask, ctypes.c_uint8), _ptr(order, ctypes.c_int32),
+                                _ptr(check, ctypes.c_uint8))
+    if r < 0:
+        raise ValueError("ring bond among the rotatable bonds")
+    return dict(c=c[:T], b=bb[:T], depth=depth[:T], mask=mask[:T * l].reshape(T, l).astype(bool), order=order[:T],
+                check=check.reshape(l, l).astype(bool))
+
+
+def dof_apply(batch, b, x, q):
+    """Pose z = g + R(omega)(tau(x) - g) + t for ligand b: q = (t, omega, theta_1..theta_T)."""
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+    q = np.ascontiguousarray(q, np.float64)
+    z = np.zeros_like(x)
+    keep = []
+    L = _ligands(batch, None, keep)
+    if _load().oracle_dof_apply(ctypes.byref(L), int(b), _ptr(x, ctypes.c_double), _ptr(q, ctypes.c_double),
+                                _ptr(z, ctypes.c_double)) != 0:
+        raise ValueError("ring bond among the rotatable bonds")
+    return z
+
+
+def dof_grad(batch, b, x, q, p):
+    """d f / d q at z = dof_apply(x, q), given p = d f / d z (shape (l, 3))."""
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+    q = np.ascontiguousarray(q, np.float64)
+    p = np.ascontiguousarray(p, np.float64).reshape(-1, 3)
+    G = np.zeros(len(q), np.float64)
+    keep = []
+    L = _ligands(batch, None, keep)
+    if _load().oracle_dof_grad(ctypes.byref(L), int(b), _ptr(x, ctypes.c_double), _ptr(q, ctypes.c_double),
+                               _ptr(p, ctypes.c_double), _ptr(G, ctypes.c_double)) != 0:
+        raise ValueError("ring bond among the rotatable bonds")
+    return G
+
+
+def refine(opk: OraclePocket, batch, xyz_in, steps=20, clip=1, bump_thr=2.0, force_accept=None, amb_delta=0.0,
+           amb_bump=0.0, amb_rel=0.0, nthreads=None, lambda0=LAMBDA0, lambda_max=LAMBDA_MAX, grow=GROW,
+           shrink=SHRINK):
+    """Local refinement (trilinear Eq. 1, gradient ascent over rigid DOF and torsions) from xyz_in (Å)."""
+    n = batch.n
+    natoms = int(batch.atom_off[-1])
+    x = np.ascontiguousarray(xyz_in, np.float64).reshape(natoms, 3)
+    _, t = batch.sizes()
+    gstride = 6 + (int(t.max()) if n else 0)
+    ns = n * steps
+    res = dict(S_start=np.zeros(n), S_final=np.zeros(n), status=np.zeros(n, np.int32), xyz=np.zeros((natoms, 3)),
+               G=np.zeros(ns * gstride), D=np.zeros(ns), lam=np.zeros(ns), S_new=np.zeros(ns),
+               verdict=np.zeros(ns, np.int32), accept=np.zeros(ns, np.int32), flags=np.zeros(ns, np.int32),
+               gstride=gstride)
+    o = RefineOut()
+    for k in ("S_start", "S_final", "xyz", "G", "D", "lam", "S_new"):
+        setattr(o, k, _ptr(res[k], ctypes.c_double))
+    for k in ("status", "verdict", "accept", "flags"):
+        setattr(o, k, _ptr(res[k], ctypes.c_int32))
+    o.gstride = gstride
+    keep = []
+    if force_accept is not None:
+        fa = np.ascontiguousarray(force_accept, np.int32)
+        assert fa.shape == (ns,)
+        keep.append(fa)
+        o.force_accept = _ptr(fa, ctypes.c_int32)
+    k = RefineKnobs(int(steps), int(clip), float(bump_thr), float(lambda0), float(lambda_max), float(grow),
+                    float(shrink), float(amb_delta), float(amb_bump), float(amb_rel))
+    g = opk.cstruct()
+    L = _ligands(batch, None, keep)
+    rc = _load().oracle_refine(ctypes.byref(g), ctypes.byref(L), ctypes.byref(k), _ptr(x, ctypes.c_double),
+                               ctypes.byref(o), int(nthreads or os.cpu_count() or 1))
+    if rc != 0:
+        raise ValueError("oracle_refine: bad knobs")
+    res["G"] = res["G"].reshape(n, steps, gstride) if ns else res["G"]
     return res

@@ -31,6 +31,12 @@
 //   - The bump check tests every pair (i in M minus {c}, j in F minus {b}):
 //     exactly the pairs whose distance changes under the torsion; a pair
 //     closer than bump_thr makes the candidate infeasible.
+//   - Local refinement (not in the paper; it only mentions steepest descent
+//     loosely): gradient ascent of the trilinear form of Eq. 1 over 3
+//     translations, 3 rotations about the centroid (exponential map) and every
+//     torsion (the side away from atom 0 moves; deltas applied from the
+//     deepest bond to the root), each step accepted only if S drops and the
+//     pose stays bump-free (and inside the box with clip_box=1).
 //   - "Pose clipping": with clip_box=1 a candidate with a moving atom outside
 //     the grid box is infeasible and an initial pose with any atom outside is
 //     skipped; with clip_box=0 the lookup is clamped to the box and the
@@ -118,6 +124,32 @@ struct or_out {
     double* cand_hi;
     int32_t* cand_status;    // 1 feasible, 0 bump, -1 outside box, -2 no such candidate
     int32_t* cand_amb;       // bit0 score interval, bit1 bump band, bit2 box band
+};
+
+// Local refinement knobs and outputs (trilinear score, gradient ascent).
+struct or_refine_knobs {
+    int steps, clip_box;
+    double bump_thr;
+    double lambda0, lambda_max, grow, shrink;  // step length (max atom displacement, Å) and its update
+    double amb_delta, amb_bump, amb_rel;       // parity bands (grid units, Å^2, relative S)
+};
+
+struct or_refine_out {
+    // per ligand
+    double* S_start;   // trilinear S of the start pose (grid units)
+    double* S_final;
+    int32_t* status;   // 0 refined, 1 skipped (start pose outside the box with clip_box=1)
+    double* xyz;       // final coordinates, Å, atom_off[b]*3 (nullable)
+    // per (ligand, step), index b*steps + s (all nullable)
+    int32_t gstride;   // stride of G: 6 + the largest torsion count
+    double* G;         // d o / d (t, omega, theta) at the step's start pose
+    double* D;         // largest atom displacement per unit of G (Å)
+    double* lambda;    // step length used
+    double* S_new;     // S of the trial pose
+    int32_t* verdict;  // bit0 S_new < S, bit1 bump-free, bit2 inside the box
+    int32_t* accept;   // the committed decision
+    int32_t* flags;    // bit0 |S_new - S| within amb_rel S, bit1 pair in the bump band, bit2 atom in the box band
+    const int32_t* force_accept;  // replay: commit these decisions instead of the own ones
 };
 
 }  // extern "C"
@@ -633,6 +665,295 @@ void dock_ligand(const Ctx& C, int b) {
     if (O.best_score) O.best_score[b] = best_p < 0 ? 0.0 : double(m.l) / (h2 * best_S);
 }
 
+
+// ------------------------------------------------ local refinement (not in the paper)
+
+Mol load_mol(const or_ligands& L, int b, std::vector<V3>* x0 = nullptr) {
+    Mol m;
+    int a0 = L.atom_off[b];
+    m.l = L.atom_off[b + 1] - a0;
+    for (int i = 0; i < m.l; ++i)
+        m.x0.push_back({double(L.xyz[3 * (a0 + i)]), double(L.xyz[3 * (a0 + i) + 1]), double(L.xyz[3 * (a0 + i) + 2])});
+    m.adj.assign(m.l, {});
+    for (int e = L.bond_off[b]; e < L.bond_off[b + 1]; ++e) {
+        int u = L.bonds[2 * e], v = L.bonds[2 * e + 1];
+        m.bonds.push_back({u, v});
+        m.adj[u].push_back(v);
+        m.adj[v].push_back(u);
+    }
+    for (int r = L.rot_off[b]; r < L.rot_off[b + 1]; ++r) m.rot.push_back(L.rot[r]);
+    if (x0) *x0 = m.x0;
+    return m;
+}
+
+// Trilinear term of one atom at grid position t with its gradient dD/dt
+// (grid units). Outside the box the term is taken at the clamped position; with
+// clip_box=0 the squared excess is added, so its gradient is 2 (t - clamp(t)).
+double trilinear_grad(const Grid& G, const V3& t, bool clip, V3& dD, bool& inside) {
+    double tc[3], f[3];
+    int i0[3];
+    bool out_axis[3];
+    double excess2 = 0.0;
+    inside = true;
+    for (int a = 0; a < 3; ++a) {
+        double hi_edge = G.n[a] - 1;
+        tc[a] = std::min(std::max(t[a], 0.0), hi_edge);
+        out_axis[a] = t[a] < 0.0 || t[a] > hi_edge;
+        if (out_axis[a]) inside = false;
+        excess2 += (t[a] - tc[a]) * (t[a] - tc[a]);
+        i0[a] = std::min(int(std::floor(tc[a])), G.n[a] - 2);
+        f[a] = tc[a] - i0[a];
+    }
+    double D = 0.0;
+    dD = {0, 0, 0};
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                double K = G.at(i0[0] + dx, i0[1] + dy, i0[2] + dz);
+                double wx = dx ? f[0] : 1.0 - f[0], wy = dy ? f[1] : 1.0 - f[1], wz = dz ? f[2] : 1.0 - f[2];
+                double sx = dx ? 1.0 : -1.0, sy = dy ? 1.0 : -1.0, sz = dz ? 1.0 : -1.0;
+                D += wx * wy * wz * K;
+                dD[0] += sx * wy * wz * K;
+                dD[1] += wx * sy * wz * K;
+                dD[2] += wx * wy * sz * K;
+            }
+    for (int a = 0; a < 3; ++a)
+        if (out_axis[a]) dD[a] = clip ? 0.0 : 2.0 * (t[a] - tc[a]);
+    if (!clip && !inside) D += excess2;
+    return D;
+}
+
+// Torsion degrees of freedom: for every rotatable bond (in the ligand's order)
+// the side away from atom 0 moves about the axis from b to c (c in the moving
+// side). Deltas are applied from the deepest bond (depth of c from atom 0) to
+// the root, ties in bond order.
+struct Torsion {
+    std::vector<char> M;
+    int c, b, depth;
+};
+struct Dofs {
+    std::vector<Torsion> tor;
+    std::vector<int> order;
+    std::vector<std::vector<char>> check;  // pairs tested by the bump check
+};
+
+Dofs dofs_of(const Mol& m) {
+    Dofs d;
+    std::vector<int> depth(m.l, -1);
+    std::vector<int> queue{0};
+    depth[0] = 0;
+    for (size_t h = 0; h < queue.size(); ++h)
+        for (int v : m.adj[queue[h]])
+            if (depth[v] < 0) { depth[v] = depth[queue[h]] + 1; queue.push_back(v); }
+    d.check.assign(m.l, std::vector<char>(m.l, 0));
+    for (int r : m.rot) {
+        int u = m.bonds[r][0], v = m.bonds[r][1];
+        std::vector<char> root_side = component(m, 0, r);
+        Torsion t;
+        t.c = root_side[u] ? v : u;
+        t.b = root_side[u] ? u : v;
+        t.M.assign(m.l, 0);
+        for (int i = 0; i < m.l; ++i) t.M[i] = !root_side[i];
+        t.depth = depth[t.c];
+        // the pairs whose distance this torsion changes (Alg. 1's bump pairs)
+        for (int i = 0; i < m.l; ++i)
+            for (int j = 0; j < m.l; ++j)
+                if (t.M[i] && i != t.c && !t.M[j] && j != t.b) d.check[i][j] = d.check[j][i] = 1;
+        d.tor.push_back(t);
+    }
+    for (int k = 0; k < int(d.tor.size()); ++k) d.order.push_back(k);
+    std::stable_sort(d.order.begin(), d.order.end(), [&](int a, int b) { return d.tor[a].depth > d.tor[b].depth; });
+    return d;
+}
+
+V3 centroid(const std::vector<V3>& x) {
+    V3 g{0, 0, 0};
+    for (const V3& xi : x) g = add(g, xi);
+    return mul(g, 1.0 / double(x.size()));
+}
+
+// Rotation matrix of the rotation vector w (Rodrigues' formula).
+std::array<double, 9> expmap(const V3& w) {
+    double th = norm(w);
+    std::array<double, 9> R{1, 0, 0, 0, 1, 0, 0, 0, 1};
+    if (th == 0.0) return R;
+    V3 k = mul(w, 1.0 / th);
+    double c = std::cos(th), s = std::sin(th), C = 1.0 - c;
+    R = {c + k[0] * k[0] * C,        k[0] * k[1] * C - k[2] * s, k[0] * k[2] * C + k[1] * s,
+         k[1] * k[0] * C + k[2] * s, c + k[1] * k[1] * C,        k[1] * k[2] * C - k[0] * s,
+         k[2] * k[0] * C - k[1] * s, k[2] * k[1] * C + k[0] * s, c + k[2] * k[2] * C};
+    return R;
+}
+
+// z = g + R(omega) (tau(x) - g) + t, with tau the torsion deltas and g the centroid of x.
+std::vector<V3> dof_apply(const Dofs& d, const std::vector<V3>& x, const double* q) {
+    std::vector<V3> y = x;
+    for (int k : d.order) {
+        const Torsion& t = d.tor[k];
+        V3 c = y[t.c], axis = sub(y[t.c], y[t.b]);
+        axis = mul(axis, 1.0 / norm(axis));
+        for (size_t i = 0; i < y.size(); ++i)
+            if (t.M[i] && int(i) != t.c) y[i] = rotate(y[i], c, axis, q[6 + k]);
+    }
+    V3 g = centroid(x);
+    std::array<double, 9> R = expmap({q[3], q[4], q[5]});
+    std::vector<V3> z(y.size());
+    for (size_t i = 0; i < y.size(); ++i) {
+        V3 v = sub(y[i], g);
+        z[i] = add(add(g, {R[0] * v[0] + R[1] * v[1] + R[2] * v[2], R[3] * v[0] + R[4] * v[1] + R[5] * v[2],
+                           R[6] * v[0] + R[7] * v[1] + R[8] * v[2]}),
+                   {q[0], q[1], q[2]});
+    }
+    return z;
+}
+
+// d f / d q from p_i = d f / d z_i at the pose z = dof_apply(x, q):
+//   translation: sum_i p_i;
+//   rotation: J(omega)^T sum_i (z_i - g - t) x p_i, J the left Jacobian of the
+//     exponential map, I + (1 - cos a)/a^2 [w]x + (a - sin a)/a^3 [w]x^2 (a = |w|);
+//   torsion k: axis_k . sum_{i in M_k} (z_i - z_c) x p_i, with the axis and c
+//     taken in z (a later rigid motion of bond k's side carries its axis along).
+void dof_grad(const Dofs& d, const std::vector<V3>& x, const double* q, const std::vector<V3>& z,
+              const std::vector<V3>& p, double* G) {
+    V3 g = centroid(x), t{q[0], q[1], q[2]}, w{q[3], q[4], q[5]};
+    V3 gt{0, 0, 0}, tau{0, 0, 0};
+    for (size_t i = 0; i < z.size(); ++i) {
+        gt = add(gt, p[i]);
+        tau = add(tau, cross(sub(sub(z[i], g), t), p[i]));
+    }
+    double a = norm(w), A, B;
+    if (a < 1e-4) {
+        A = 0.5 - a * a / 24.0;
+        B = 1.0 / 6.0 - a * a / 120.0;
+    } else {
+        A = (1.0 - std::cos(a)) / (a * a);
+        B = (a - std::sin(a)) / (a * a * a);
+    }
+    // J^T v = v - A (w x v) + B (w x (w x v))   ([w]x^T = -[w]x)
+    V3 wv = cross(w, tau), wwv = cross(w, wv);
+    V3 gw = add(sub(tau, mul(wv, A)), mul(wwv, B));
+    for (int a3 = 0; a3 < 3; ++a3) {
+        G[a3] = gt[a3];
+        G[3 + a3] = gw[a3];
+    }
+    for (size_t k = 0; k < d.tor.size(); ++k) {
+        const Torsion& tk = d.tor[k];
+        V3 axis = sub(z[tk.c], z[tk.b]);
+        axis = mul(axis, 1.0 / norm(axis));
+        V3 s{0, 0, 0};
+        for (size_t i = 0; i < z.size(); ++i)
+            if (tk.M[i]) s = add(s, cross(sub(z[i], z[tk.c]), p[i]));
+        G[6 + k] = dot(axis, s);
+    }
+}
+
+// Trilinear S of a pose with dS/dz (grid units per Å) and the box flags.
+double score_grad(const Grid& G, const std::vector<V3>& z, bool clip, double delta, std::vector<V3>* dS, bool& inside,
+                  bool& box_amb) {
+    double S = 0.0;
+    inside = true;
+    box_amb = false;
+    if (dS) dS->assign(z.size(), {0, 0, 0});
+    for (size_t i = 0; i < z.size(); ++i) {
+        V3 t = G.to_grid(z[i]);
+        V3 dD;
+        bool in;
+        S += trilinear_grad(G, t, clip, dD, in);
+        inside = inside && in;
+        for (int a = 0; a < 3; ++a)
+            if (delta > 0.0 && (std::fabs(t[a]) <= delta || std::fabs(t[a] - (G.n[a] - 1)) <= delta)) box_amb = true;
+        if (dS) (*dS)[i] = mul(dD, 1.0 / G.g->h);
+    }
+    return S;
+}
+
+void refine_ligand(const Grid& G, const or_ligands& L, const or_refine_knobs& K, const double* xyz_in,
+                   or_refine_out& O, int b) {
+    Mol m = load_mol(L, b);
+    Dofs d = dofs_of(m);
+    const int a0 = L.atom_off[b];
+    const bool clip = K.clip_box != 0;
+    const double h2 = G.g->h * G.g->h, thr2 = K.bump_thr * K.bump_thr;
+    const int T = int(d.tor.size());
+    std::vector<V3> z(m.l);
+    for (int i = 0; i < m.l; ++i) z[i] = {xyz_in[3 * (a0 + i)], xyz_in[3 * (a0 + i) + 1], xyz_in[3 * (a0 + i) + 2]};
+    bool inside, box_amb;
+    std::vector<V3> dS;
+    double S = score_grad(G, z, clip, 0.0, nullptr, inside, box_amb);
+    if (O.S_start) O.S_start[b] = S;
+    const bool skip = clip && !inside;
+    if (O.status) O.status[b] = skip ? 1 : 0;
+    double lambda = K.lambda0;
+    std::vector<double> Gq(6 + T), q(6 + T);
+    for (int st = 0; st < K.steps && !skip; ++st) {
+        const int64_t si = int64_t(b) * K.steps + st;
+        score_grad(G, z, clip, 0.0, &dS, inside, box_amb);
+        // o = l / (h^2 S): d o / d z_i = -l / (h^2 S^2) dS/dz_i
+        std::vector<V3> p(m.l);
+        for (int i = 0; i < m.l; ++i) p[i] = mul(dS[i], -double(m.l) / (h2 * S * S));
+        std::vector<double> zero(6 + T, 0.0);
+        dof_grad(d, z, zero.data(), z, p, Gq.data());
+        // largest first-order atom displacement per unit of G
+        V3 g = centroid(z);
+        double D = 0.0;
+        for (int i = 0; i < m.l; ++i) {
+            V3 di = add({Gq[0], Gq[1], Gq[2]}, cross({Gq[3], Gq[4], Gq[5]}, sub(z[i], g)));
+            for (int k = 0; k < T; ++k) {
+                const Torsion& tk = d.tor[k];
+                if (!tk.M[i]) continue;
+                V3 axis = sub(z[tk.c], z[tk.b]);
+                axis = mul(axis, 1.0 / norm(axis));
+                di = add(di, mul(cross(axis, sub(z[i], z[tk.c])), Gq[6 + k]));
+            }
+            D = std::max(D, norm(di));
+        }
+        if (O.G)
+            for (int k = 0; k < 6 + T; ++k) O.G[si * O.gstride + k] = Gq[k];
+        if (O.D) O.D[si] = D;
+        if (O.lambda) O.lambda[si] = lambda;
+        int verdict = 0, flags = 0;
+        double S_new = S;
+        std::vector<V3> zn;
+        if (D > 0.0) {
+            for (int k = 0; k < 6 + T; ++k) q[k] = Gq[k] * (lambda / D);
+            zn = dof_apply(d, z, q.data());
+            bool in_new;
+            S_new = score_grad(G, zn, clip, K.amb_delta, nullptr, in_new, box_amb);
+            bool clash = false;
+            for (int i = 0; i < m.l; ++i)
+                for (int j = i + 1; j < m.l; ++j) {
+                    if (!d.check[i][j]) continue;
+                    V3 dv = sub(zn[i], zn[j]);
+                    double d2 = dot(dv, dv);
+                    if (d2 < thr2) clash = true;
+                    if (K.amb_bump > 0 && std::fabs(d2 - thr2) <= K.amb_bump) flags |= 2;
+                }
+            if (S_new < S) verdict |= 1;
+            if (!clash) verdict |= 2;
+            if (in_new) verdict |= 4;
+            if (K.amb_rel > 0 && std::fabs(S_new - S) <= K.amb_rel * S) flags |= 1;
+            if (box_amb) flags |= 4;
+        }
+        int acc = (verdict & 1) && (verdict & 2) && (!clip || (verdict & 4));
+        if (O.force_accept) acc = O.force_accept[si] && D > 0.0;
+        if (O.S_new) O.S_new[si] = S_new;
+        if (O.verdict) O.verdict[si] = verdict;
+        if (O.accept) O.accept[si] = acc;
+        if (O.flags) O.flags[si] = flags;
+        if (acc) {
+            z = zn;
+            S = S_new;
+            lambda = std::min(lambda * K.grow, K.lambda_max);
+        } else {
+            lambda *= K.shrink;
+        }
+    }
+    if (O.S_final) O.S_final[b] = S;
+    if (O.xyz)
+        for (int i = 0; i < m.l; ++i)
+            for (int a = 0; a < 3; ++a) O.xyz[3 * (a0 + i) + a] = z[i][a];
+}
+
 }  // namespace
 
 extern "C" {
@@ -695,6 +1016,89 @@ int oracle_dock(const or_grid* g, const or_ligands* L, const or_knobs* k, or_out
     std::atomic<int> next{0};
     auto worker = [&]() {
         for (int b = next++; b < L->n; b = next++) dock_ligand(C, b);
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nthreads; ++t) pool.emplace_back(worker);
+    worker();
+    for (auto& t : pool) t.join();
+    return 0;
+}
+
+// Trilinear S (grid units), dS/dx (grid units per Å) and the inside flag of one conformation.
+int oracle_trilinear_grad(const or_grid* g, int clip, const double* xyz, int natoms, double* S, double* dSdx,
+                          int* inside) {
+    Grid G{g, {g->nx, g->ny, g->nz}};
+    std::vector<V3> z(natoms), dS;
+    for (int i = 0; i < natoms; ++i) z[i] = {xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]};
+    bool in, amb;
+    *S = score_grad(G, z, clip != 0, 0.0, &dS, in, amb);
+    for (int i = 0; i < natoms; ++i)
+        for (int a = 0; a < 3; ++a) dSdx[3 * i + a] = dS[i][a];
+    *inside = in ? 1 : 0;
+    return 0;
+}
+
+// Torsion layout of ligand b: per rotatable bond (ligand order) c, b, depth and
+// the moving mask (l entries each); order = application order. Returns T or -1.
+int oracle_torsions(const or_ligands* L, int b, int32_t* c, int32_t* bb, int32_t* depth, uint8_t* mask,
+                    int32_t* order, uint8_t* check) {
+    Mol m = load_mol(*L, b);
+    std::vector<Side> sides;
+    if (!sides_of(m, sides)) return -1;
+    Dofs d = dofs_of(m);
+    for (size_t k = 0; k < d.tor.size(); ++k) {
+        c[k] = d.tor[k].c;
+        bb[k] = d.tor[k].b;
+        depth[k] = d.tor[k].depth;
+        for (int i = 0; i < m.l; ++i) mask[k * m.l + i] = uint8_t(d.tor[k].M[i]);
+        order[k] = d.order[k];
+    }
+    if (check)
+        for (int i = 0; i < m.l; ++i)
+            for (int j = 0; j < m.l; ++j) check[i * m.l + j] = uint8_t(d.check[i][j]);
+    return int(d.tor.size());
+}
+
+// z = dof_apply(x, q) for ligand b (x: l x 3 Å, q: 6 + T).
+int oracle_dof_apply(const or_ligands* L, int b, const double* x, const double* q, double* z) {
+    Mol m = load_mol(*L, b);
+    std::vector<Side> sides;
+    if (!sides_of(m, sides)) return -1;
+    Dofs d = dofs_of(m);
+    std::vector<V3> xv(m.l);
+    for (int i = 0; i < m.l; ++i) xv[i] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+    std::vector<V3> zv = dof_apply(d, xv, q);
+    for (int i = 0; i < m.l; ++i)
+        for (int a = 0; a < 3; ++a) z[3 * i + a] = zv[i][a];
+    return 0;
+}
+
+// d f / d q of ligand b from p = d f / d z at z = dof_apply(x, q).
+int oracle_dof_grad(const or_ligands* L, int b, const double* x, const double* q, const double* p, double* G) {
+    Mol m = load_mol(*L, b);
+    std::vector<Side> sides;
+    if (!sides_of(m, sides)) return -1;
+    Dofs d = dofs_of(m);
+    std::vector<V3> xv(m.l), pv(m.l);
+    for (int i = 0; i < m.l; ++i) {
+        xv[i] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+        pv[i] = {p[3 * i], p[3 * i + 1], p[3 * i + 2]};
+    }
+    std::vector<V3> zv = dof_apply(d, xv, q);
+    dof_grad(d, xv, q, zv, pv, G);
+    return 0;
+}
+
+// Local refinement of every ligand of the batch from the start poses xyz_in
+// (Å, atom_off layout), trilinear score.
+int oracle_refine(const or_grid* g, const or_ligands* L, const or_refine_knobs* k, const double* xyz_in,
+                  or_refine_out* o, int nthreads) {
+    if (k->steps < 0 || !(k->lambda0 > 0) || !(k->bump_thr >= 0)) return -1;
+    Grid G{g, {g->nx, g->ny, g->nz}};
+    if (nthreads < 1) nthreads = 1;
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+        for (int b = next++; b < L->n; b = next++) refine_ligand(G, *L, *k, xyz_in, *o, b);
     };
     std::vector<std::thread> pool;
     for (int t = 1; t < nthreads; ++t) pool.emplace_back(worker);
