@@ -117,7 +117,7 @@ typedef struct {
  *   bump_thr           Å; a candidate is infeasible when an atom pair whose
  *                      distance depends on the torsion is closer than this
  *   score_mode         0 nearest voxel, 1 trilinear interpolation of K
- *   refine_steps       0; gradient refinement is a separate call
+ *   refine_steps       ascent steps of dock_refine (0..1000); dock_run ignores it
  *   seed               seed of the initial orientations
  *   plain_mode         1: one launch per (pocket, ligand) pair, no bucketing
  *                      and no graph (the comparison form); 0: batched */
@@ -294,6 +294,100 @@ int dock_last_stats(const dock_ctx* ctx, dock_stats* s);
  * them ordered. dock_last_stats is not updated by this call. */
 int dock_run_static(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs* k, dock_result* out,
                     float* xyz_out, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Local refinement and the differentiable score (not in the paper, which
+ * only mentions steepest descent; built on the trilinear form of Eq. 1).
+ *
+ * Score: S = sum_i D(x_i), D the trilinear interpolant of K between voxel
+ * centres (grid units); outside the box D is taken at the clamped position,
+ * plus the squared excess in grid units when clipping is off;
+ * o = l / (h^2 S) (Å^-2).
+ *
+ * Pose degrees of freedom of ligand b: q = (t, omega, theta_1..theta_T),
+ * T = its rotatable bonds in the batch's order. theta_k turns the side of
+ * bond k away from atom 0 about the axis from the bond's other atom to its
+ * own bond atom (right-handed), deepest bond first; then the pose rotates by
+ * the rotation vector omega (radians) about the centroid g of the input
+ * coordinates x and moves by t (Å):  z = g + R(omega) (tau(x) - g) + t.
+ *
+ * Every pointer below is device memory; calls are asynchronous on `stream`
+ * unless stated otherwise. Coordinates use the batch's atom_off layout
+ * (3 floats per atom, Å), per pocket where a call takes several pockets
+ * (pocket-major, as dock_run's xyz_out).
+ * ------------------------------------------------------------------------ */
+
+/* Ligand count, atom count, largest ligand and largest torsion count of a
+ * batch (host pointers; any may be NULL). q arrays use a stride of at least
+ * 6 + tmax floats per ligand. */
+int dock_batch_info(dock_ctx* ctx, int batch_id, int* n, int* natoms, int* lmax, int* tmax);
+
+/* o per ligand (n floats) of the poses xyz on one pocket. clip: 1 the
+ * box-clamped interpolant, 0 plus the outside penalty. */
+int dock_score_trilinear(dock_ctx* ctx, int batch_id, int pocket_id, int clip, const float* xyz, float* o,
+                         void* stream);
+
+/* Adjoint of dock_score_trilinear: grad_xyz (3 * natoms floats) =
+ * grad_o[b] * d o_b / d x_i, with grad_o NULL meaning ones. */
+int dock_score_trilinear_grad(dock_ctx* ctx, int batch_id, int pocket_id, int clip, const float* xyz,
+                              const float* grad_o, float* grad_xyz, void* stream);
+
+/* z = the pose x moved by q (n * qstride floats, qstride >= 6 + tmax). */
+int dock_dof_apply(dock_ctx* ctx, int batch_id, const float* x, const float* q, int qstride, float* z, void* stream);
+
+/* Adjoint of dock_dof_apply at (x, q): grad_q = J(q)^T grad_z, where
+ *   d/dt = sum_i g_i,  d/domega = Jl(omega)^T sum_i (z_i - g - t) x g_i
+ *   (Jl the left Jacobian of the exponential map), d/dtheta_k = axis_k .
+ *   sum over the moving side of (z_i - z_c) x g_i with the axis taken in z.
+ * Slots of grad_q past 6 + T_b are set to 0. */
+int dock_dof_grad(dock_ctx* ctx, int batch_id, const float* x, const float* q, int qstride, const float* grad_z,
+                  float* grad_q, void* stream);
+
+/* Local refinement of one pose per (pocket, ligand): k->refine_steps steps
+ * of gradient ascent on the trilinear o from the poses xyz_in (e.g. dock_run's
+ * xyz_out). A step moves along d o / d q, scaled so that the largest
+ * first-order atom displacement is lambda Å; it is kept only if S drops, no
+ * pair moved by a torsion (Alg. 1's bump pairs, all rotatable bonds) comes
+ * closer than k->bump_thr, and (k->clip_box) every atom stays inside the
+ * box. lambda starts at 0.25 Å, grows by 1.5 after a kept step (at most
+ * 1 Å) and halves after a rejected one. Pairs whose start pose lies outside
+ * the box with clipping on are returned unchanged with status 1.
+ *   xyz_in, xyz_out   npockets * 3 * atom_off[n] floats (may alias: no)
+ *   out               npockets * n results: score = refined o, pose = -1,
+ *                     status 0 refined / 1 skipped
+ *   on_device         1: every pointer is device memory, the call returns
+ *                     at once; 0: host memory, the call waits
+ * Uses k->refine_steps, k->clip_box and k->bump_thr; the trilinear score
+ * regardless of k->score_mode. */
+int dock_refine(dock_ctx* ctx, int batch_id, const int32_t* pocket_ids, int npockets, const dock_knobs* k,
+                const float* xyz_in, dock_result* out, float* xyz_out, int on_device, void* stream);
+
+/* Per-step record of dock_refine on one pocket, host arrays, for parity
+ * checks. Index of (ligand b, step s): b * steps + s.
+ *   gstride   stride of G (>= 6 + tmax)
+ *   G         d o / d q at the step's start pose (n * steps * gstride)
+ *   D         largest first-order atom displacement per unit of G (Å)
+ *   lam       step length used (Å)
+ *   S_new     S of the trial pose (grid units)
+ *   verdict   bit0 S_new < S, bit1 bump-free, bit2 inside the box
+ *   accept    1 when the trial pose was kept
+ *   S_start, S_final, status   per ligand */
+typedef struct {
+    int32_t gstride;
+    float* G;
+    float* D;
+    float* lam;
+    float* S_new;
+    int32_t* verdict;
+    int32_t* accept;
+    float* S_start;
+    float* S_final;
+    int32_t* status;
+} dock_refine_trace_buf;
+
+/* dock_refine on one pocket with the record above. Host arrays, synchronous. */
+int dock_refine_trace(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs* k, const float* xyz_in,
+                      const dock_refine_trace_buf* tr, dock_result* out, float* xyz_out);
 
 #ifdef __cplusplus
 }

@@ -79,7 +79,7 @@ class RefineOut(ctypes.Structure):
                 ("xyz", P(ctypes.c_double)), ("gstride", ctypes.c_int32), ("G", P(ctypes.c_double)),
                 ("D", P(ctypes.c_double)), ("lam", P(ctypes.c_double)), ("S_new", P(ctypes.c_double)),
                 ("verdict", P(ctypes.c_int32)), ("accept", P(ctypes.c_int32)), ("flags", P(ctypes.c_int32)),
-                ("force_accept", P(ctypes.c_int32))]
+                ("force_accept", P(ctypes.c_int32)), ("force_G", P(ctypes.c_double))]
 
 
 # Step-length rule of the local refinement (largest atom displacement, Å):
@@ -368,10 +368,14 @@ def dof_grad(batch, b, x, q, p):
     return G
 
 
-def refine(opk: OraclePocket, batch, xyz_in, steps=20, clip=1, bump_thr=2.0, force_accept=None, amb_delta=0.0,
-           amb_bump=0.0, amb_rel=0.0, nthreads=None, lambda0=LAMBDA0, lambda_max=LAMBDA_MAX, grow=GROW,
+def refine(opk: OraclePocket, batch, xyz_in, steps=20, clip=1, bump_thr=2.0, force_accept=None, force_G=None,
+           amb_delta=0.0, amb_bump=0.0, amb_rel=0.0, nthreads=None, lambda0=LAMBDA0, lambda_max=LAMBDA_MAX, grow=GROW,
            shrink=SHRINK):
-    """Local refinement (trilinear Eq. 1, gradient ascent over rigid DOF and torsions) from xyz_in (Å)."""
+    """Local refinement (trilinear Eq. 1, gradient ascent over rigid DOF and torsions) from xyz_in (Å).
+
+    Replay: force_accept commits given decisions; force_G (n, steps, >= 6 + T) gives the step direction where
+    an atom of the step's start pose lies within amb_delta of a cell face (flag bit 3), where the gradient of
+    the trilinear score is one-sided and either side is valid."""
     n = batch.n
     natoms = int(batch.atom_off[-1])
     x = np.ascontiguousarray(xyz_in, np.float64).reshape(natoms, 3)
@@ -394,6 +398,13 @@ def refine(opk: OraclePocket, batch, xyz_in, steps=20, clip=1, bump_thr=2.0, for
         assert fa.shape == (ns,)
         keep.append(fa)
         o.force_accept = _ptr(fa, ctypes.c_int32)
+    if force_G is not None and ns:
+        fg = np.zeros((n, steps, gstride))
+        src = np.asarray(force_G, np.float64)
+        fg[:, :, :min(gstride, src.shape[-1])] = src.reshape(n, steps, -1)[:, :, :gstride]
+        fg = np.ascontiguousarray(fg.reshape(-1))
+        keep.append(fg)
+        o.force_G = _ptr(fg, ctypes.c_double)
     k = RefineKnobs(int(steps), int(clip), float(bump_thr), float(lambda0), float(lambda_max), float(grow),
                     float(shrink), float(amb_delta), float(amb_bump), float(amb_rel))
     g = opk.cstruct()

@@ -148,8 +148,10 @@ struct or_refine_out {
     double* S_new;     // S of the trial pose
     int32_t* verdict;  // bit0 S_new < S, bit1 bump-free, bit2 inside the box
     int32_t* accept;   // the committed decision
-    int32_t* flags;    // bit0 |S_new - S| within amb_rel S, bit1 pair in the bump band, bit2 atom in the box band
+    int32_t* flags;    // bit0 |S_new - S| within amb_rel S, bit1 pair in the bump band, bit2 atom in the box band,
+                       // bit3 an atom of the step's start pose within amb_delta of a cell face (one-sided gradients)
     const int32_t* force_accept;  // replay: commit these decisions instead of the own ones
+    const double* force_G;        // replay: the step direction to use where bit3 is set (same layout as G)
 };
 
 }  // extern "C"
@@ -893,6 +895,17 @@ void refine_ligand(const Grid& G, const or_ligands& L, const or_refine_knobs& K,
         for (int i = 0; i < m.l; ++i) p[i] = mul(dS[i], -double(m.l) / (h2 * S * S));
         std::vector<double> zero(6 + T, 0.0);
         dof_grad(d, z, zero.data(), z, p, Gq.data());
+        // the trilinear gradient is one-sided on a cell face: either side is a valid gradient
+        int flags = 0;
+        for (int i = 0; i < m.l && K.amb_delta > 0; ++i) {
+            V3 t = G.to_grid(z[i]);
+            for (int a = 0; a < 3; ++a)
+                if (std::fabs(t[a] - std::round(t[a])) <= K.amb_delta) flags |= 8;
+        }
+        if (O.G)
+            for (int k = 0; k < 6 + T; ++k) O.G[si * O.gstride + k] = Gq[k];
+        if ((flags & 8) && O.force_G)
+            for (int k = 0; k < 6 + T; ++k) Gq[k] = O.force_G[si * O.gstride + k];
         // largest first-order atom displacement per unit of G
         V3 g = centroid(z);
         double D = 0.0;
@@ -907,11 +920,9 @@ void refine_ligand(const Grid& G, const or_ligands& L, const or_refine_knobs& K,
             }
             D = std::max(D, norm(di));
         }
-        if (O.G)
-            for (int k = 0; k < 6 + T; ++k) O.G[si * O.gstride + k] = Gq[k];
         if (O.D) O.D[si] = D;
         if (O.lambda) O.lambda[si] = lambda;
-        int verdict = 0, flags = 0;
+        int verdict = 0;
         double S_new = S;
         std::vector<V3> zn;
         if (D > 0.0) {

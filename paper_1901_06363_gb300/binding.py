@@ -68,6 +68,12 @@ class dock_stats(ctypes.Structure):
                 ("bump_pairs", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64), ("sweep_ms", ctypes.c_double)]
 
 
+class dock_refine_trace_buf(ctypes.Structure):
+    _fields_ = [("gstride", ctypes.c_int32), ("G", ctypes.c_void_p), ("D", ctypes.c_void_p), ("lam", ctypes.c_void_p),
+                ("S_new", ctypes.c_void_p), ("verdict", ctypes.c_void_p), ("accept", ctypes.c_void_p),
+                ("S_start", ctypes.c_void_p), ("S_final", ctypes.c_void_p), ("status", ctypes.c_void_p)]
+
+
 def _load():
     if not os.path.exists(library_path):
         raise ImportError(f"{library_path} is missing: build it with `python -m paper_1901_06363_gb300.build` "
@@ -91,6 +97,15 @@ def _load():
         "dock_autotune": ([vp, ctypes.c_int, ctypes.c_int, P(dock_knobs), P(dock_tile), vp], ctypes.c_int),
         "dock_last_stats": ([vp, P(dock_stats)], ctypes.c_int),
         "dock_run_static": ([vp, ctypes.c_int, ctypes.c_int, P(dock_knobs), vp, vp, vp], ctypes.c_int),
+        "dock_batch_info": ([vp, ctypes.c_int, i32p, i32p, i32p, i32p], ctypes.c_int),
+        "dock_score_trilinear": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp], ctypes.c_int),
+        "dock_score_trilinear_grad": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp], ctypes.c_int),
+        "dock_dof_apply": ([vp, ctypes.c_int, vp, vp, ctypes.c_int, vp, vp], ctypes.c_int),
+        "dock_dof_grad": ([vp, ctypes.c_int, vp, vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
+        "dock_refine": ([vp, ctypes.c_int, P(ctypes.c_int32), ctypes.c_int, P(dock_knobs), vp, vp, vp, ctypes.c_int,
+                         vp], ctypes.c_int),
+        "dock_refine_trace": ([vp, ctypes.c_int, ctypes.c_int, P(dock_knobs), vp, P(dock_refine_trace_buf), vp, vp],
+                              ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -120,7 +135,7 @@ def knobs_struct(kn) -> dock_knobs:
     k.clip_box = int(kn.get("clip_box", 1))
     k.bump_thr = float(kn.get("bump_thr", 2.0))
     k.score_mode = int(kn.get("score_mode", 0))
-    k.refine_steps = 0
+    k.refine_steps = int(kn.get("refine_steps", 0))
     k.seed = int(kn.get("seed", 0))
     k.plain_mode = int(kn.get("plain_mode", 0))
     return k
@@ -291,3 +306,108 @@ class Docker:
         s = dock_stats()
         self._check(lib.dock_last_stats(self._c, ctypes.byref(s)), "dock_last_stats")
         return {name: getattr(s, name) for name, _ in dock_stats._fields_}
+
+    # ------------------------------------------- refinement and differentiable score
+    def batch_info(self, bid: int):
+        """(ligands, atoms, largest ligand, largest torsion count) of a batch."""
+        v = [ctypes.c_int(0) for _ in range(4)]
+        self._check(lib.dock_batch_info(self._c, bid, *[ctypes.byref(x) for x in v]), "dock_batch_info")
+        return tuple(x.value for x in v)
+
+    def score_trilinear(self, bid: int, pid: int, xyz, clip: int = 1, out=None, stream=None):
+        """o per ligand (torch CUDA tensor) of the poses xyz (CUDA float32, atom_off layout)."""
+        import torch
+        n = self.batch_info(bid)[0]
+        xyz = xyz.contiguous()
+        if out is None:
+            out = torch.empty(n, dtype=torch.float32, device=xyz.device)
+        self._check(lib.dock_score_trilinear(self._c, bid, pid, int(clip), ctypes.c_void_p(xyz.data_ptr()),
+                                             ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+                    "dock_score_trilinear")
+        return out
+
+    def score_trilinear_grad(self, bid: int, pid: int, xyz, grad_o=None, clip: int = 1, stream=None):
+        import torch
+        xyz = xyz.contiguous()
+        g = torch.empty_like(xyz)
+        go = grad_o.contiguous() if grad_o is not None else None
+        self._check(lib.dock_score_trilinear_grad(self._c, bid, pid, int(clip), ctypes.c_void_p(xyz.data_ptr()),
+                                                  ctypes.c_void_p(go.data_ptr()) if go is not None else None,
+                                                  ctypes.c_void_p(g.data_ptr()), _stream_ptr(stream)),
+                    "dock_score_trilinear_grad")
+        return g
+
+    def dof_apply(self, bid: int, x, q, stream=None):
+        """Pose z of x moved by q (CUDA float32, shape (n, qstride), qstride >= 6 + tmax)."""
+        import torch
+        x, q = x.contiguous(), q.contiguous()
+        z = torch.empty_like(x)
+        self._check(lib.dock_dof_apply(self._c, bid, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(q.data_ptr()),
+                                       q.shape[-1], ctypes.c_void_p(z.data_ptr()), _stream_ptr(stream)),
+                    "dock_dof_apply")
+        return z
+
+    def dof_grad(self, bid: int, x, q, grad_z, stream=None):
+        import torch
+        x, q, grad_z = x.contiguous(), q.contiguous(), grad_z.contiguous()
+        g = torch.empty_like(q)
+        self._check(lib.dock_dof_grad(self._c, bid, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(q.data_ptr()),
+                                      q.shape[-1], ctypes.c_void_p(grad_z.data_ptr()), ctypes.c_void_p(g.data_ptr()),
+                                      _stream_ptr(stream)), "dock_dof_grad")
+        return g
+
+    def refine(self, bid: int, pocket_ids, kn, xyz_in, out=None, xyz_out=None, stream=None):
+        """dock_refine. xyz_in a CUDA tensor: device outputs (given or allocated); numpy: host outputs."""
+        pids = np.ascontiguousarray(pocket_ids, np.int32).reshape(-1)
+        k = knobs_struct(kn)
+        n, natoms = self.batch_info(bid)[:2]
+        npk = len(pids)
+        if hasattr(xyz_in, "data_ptr"):
+            import torch
+            xyz_in = xyz_in.contiguous()
+            if out is None:
+                out = torch.empty(npk * n * 4, dtype=torch.int32, device=xyz_in.device)
+            if xyz_out is None:
+                xyz_out = torch.empty_like(xyz_in)
+            rc = lib.dock_refine(self._c, bid, _ptr(pids, ctypes.c_int32), npk, ctypes.byref(k),
+                                 ctypes.c_void_p(xyz_in.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                 ctypes.c_void_p(xyz_out.data_ptr()), 1, _stream_ptr(stream))
+        else:
+            xin = np.ascontiguousarray(xyz_in, np.float32)
+            out = np.zeros(npk * n, RESULT_DTYPE)
+            xyz_out = np.zeros((npk, natoms, 3), np.float32)
+            rc = lib.dock_refine(self._c, bid, _ptr(pids, ctypes.c_int32), npk, ctypes.byref(k),
+                                 ctypes.c_void_p(xin.ctypes.data), ctypes.c_void_p(out.ctypes.data),
+                                 ctypes.c_void_p(xyz_out.ctypes.data), 0, None)
+        self._check(rc, "dock_refine")
+        return out, xyz_out
+
+    def refine_trace(self, bid: int, pid: int, kn, xyz_in):
+        """dock_refine_trace with host buffers; returns a dict of numpy arrays."""
+        n, natoms, _, tmax = self.batch_info(bid)
+        steps = int(kn["refine_steps"])
+        gstride = 6 + tmax
+        ns = max(n * steps, 1)
+        bufs = dict(G=np.zeros(ns * gstride, np.float32), D=np.zeros(ns, np.float32), lam=np.zeros(ns, np.float32),
+                    S_new=np.zeros(ns, np.float32), verdict=np.zeros(ns, np.int32), accept=np.zeros(ns, np.int32),
+                    S_start=np.zeros(max(n, 1), np.float32), S_final=np.zeros(max(n, 1), np.float32),
+                    status=np.zeros(max(n, 1), np.int32))
+        tr = dock_refine_trace_buf()
+        tr.gstride = gstride
+        for name, a in bufs.items():
+            setattr(tr, name, a.ctypes.data)
+        xin = np.ascontiguousarray(xyz_in, np.float32)
+        out = np.zeros(n, RESULT_DTYPE)
+        xyz_out = np.zeros((natoms, 3), np.float32)
+        k = knobs_struct(kn)
+        rc = lib.dock_refine_trace(self._c, bid, pid, ctypes.byref(k), ctypes.c_void_p(xin.ctypes.data),
+                                   ctypes.byref(tr), ctypes.c_void_p(out.ctypes.data),
+                                   ctypes.c_void_p(xyz_out.ctypes.data))
+        self._check(rc, "dock_refine_trace")
+        res = {k2: (v[:n * steps] if v.shape[0] == ns and k2 not in ("S_start", "S_final", "status") else v[:n])
+               for k2, v in bufs.items() if k2 != "G"}
+        res["G"] = bufs["G"][:n * steps * gstride].reshape(n, steps, gstride)
+        res["gstride"] = gstride
+        res["result"] = out
+        res["xyz"] = xyz_out
+        return res

@@ -22,6 +22,7 @@
 #define GD_DEFINE_AUX_KERNELS
 #include "geodock_kernels.cuh"
 #include "geodock_launch.h"
+#include "geodock_refine_launch.h"
 
 using namespace gd;
 
@@ -53,6 +54,7 @@ struct PocketH {
     bool live = false;
     PocketDev d{};
     std::unique_ptr<DevBuf> K, Kp;
+    std::unique_ptr<DevBuf> dev;  // device copy of d
 };
 
 struct BatchH {
@@ -63,6 +65,9 @@ struct BatchH {
     std::vector<int> side_off;
     std::vector<int> atom_off;
     std::unique_ptr<DevBuf> lig, side, idx, xyz0;
+    // local refinement: torsions (side away from atom 0, deepest bond first) and bump-pair rows
+    int tmax = 0;
+    std::unique_ptr<DevBuf> rlig, rtor, check;
 };
 
 // Everything a batched run needs that depends on (batch, pockets, knobs, tile).
@@ -92,6 +97,8 @@ struct dock_ctx {
     dock_tile tile{0, 0, 0};           // forced shape (0 = automatic)
     std::map<std::string, dock_tile> tuned;  // autotuned shapes per (batch, knobs)
     DevBuf counter, pose_key, pose_xyz, res, xyz_res;
+    DevBuf ref_xyz_in, ref_xyz_out, ref_res;                 // host-memory form of dock_refine
+    std::map<std::string, std::unique_ptr<DevBuf>> pocket_sets;  // device pocket arrays per pocket list
     std::map<std::string, std::unique_ptr<Plan>> plans;
     dock_stats stats{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the sweep kernel(s) of the last run
@@ -165,7 +172,7 @@ int check_knobs(dock_ctx* ctx, const dock_knobs* k) {
     if (!(k->bump_thr >= 0.0) || !std::isfinite(k->bump_thr)) return fail(ctx, DOCK_ERR_INVALID_ARG, "knobs: bump_thr");
     if (!std::isfinite(k->threshold)) return fail(ctx, DOCK_ERR_INVALID_ARG, "knobs: threshold");
     if (k->score_mode != 0 && k->score_mode != 1) return fail(ctx, DOCK_ERR_INVALID_ARG, "knobs: score_mode");
-    if (k->refine_steps != 0) return fail(ctx, DOCK_ERR_UNSUPPORTED, "knobs: refinement runs through dock_refine");
+    if (k->refine_steps < 0 || k->refine_steps > 1000) return fail(ctx, DOCK_ERR_INVALID_ARG, "knobs: refine_steps");
     if (k->enable_refinement && peel_tile(k->hp_step) < 0)
         return fail(ctx, DOCK_ERR_UNSUPPORTED, "knobs: no tile size divides 360 for this step");
     return DOCK_OK;
@@ -363,6 +370,9 @@ int dock_init_pocket(dock_ctx* ctx, const dock_pocket* p, int* pocket_id) {
         ph.d.origin[a] = p->origin[a];
         ph.d.centre[a] = p->centre[a];
     }
+    ph.dev.reset(new DevBuf());
+    CK(ph.dev->ensure(sizeof(PocketDev)));
+    CK(cudaMemcpy(ph.dev->p, &ph.d, sizeof(PocketDev), cudaMemcpyHostToDevice));
     ph.live = true;
     ctx->pockets.push_back(std::move(ph));
     *pocket_id = (int)ctx->pockets.size() - 1;
@@ -389,6 +399,9 @@ int dock_upload_ligands(dock_ctx* ctx, const dock_ligand_batch* b, int* batch_id
     std::vector<LigDev> lig(b->n);
     std::vector<SideDev> sides;
     std::vector<uint8_t> idx;
+    std::vector<RefLigDev> rlig(b->n);
+    std::vector<RefTorDev> rtor;
+    std::vector<uint32_t> check;
     if (b->n > 0 && (b->atom_off[0] != 0 || b->bond_off[0] != 0 || b->rot_off[0] != 0))
         return fail(ctx, DOCK_ERR_INVALID_ARG, "batch: offsets must start at 0");
     for (int i = 0; i < b->n; ++i) {
@@ -426,6 +439,27 @@ int dock_upload_ligands(dock_ctx* ctx, const dock_ligand_batch* b, int* batch_id
         B.side_off.push_back((int)sides.size());
         B.atom_off.push_back(a0);
         B.lmax = std::max(B.lmax, l);
+        B.tmax = std::max(B.tmax, nr);
+        // graph depth from atom 0 (refinement order) and the bump-pair rows
+        std::vector<int> depth(l, -1);
+        {
+            std::vector<int> q{0};
+            depth[0] = 0;
+            for (size_t h = 0; h < q.size(); ++h)
+                for (int y : adj[q[h]])
+                    if (depth[y] < 0) {
+                        depth[y] = depth[q[h]] + 1;
+                        q.push_back(y);
+                    }
+        }
+        const int wpr = (l + 31) / 32;
+        RefLigDev& RL = rlig[i];
+        RL.tor_off = (int)rtor.size();
+        RL.T = nr;
+        RL.check_off = (int)check.size();
+        RL.wpr = wpr;
+        check.resize(check.size() + (size_t)l * wpr, 0u);
+        std::vector<std::tuple<int, int, int>> tor_depth;  // (depth of c, torsion, moving side)
         for (int r = 0; r < nr; ++r) {
             int e = b->rot[r0 + r];
             if (e < 0 || e >= ne) return fail(ctx, DOCK_ERR_INVALID_ARG, "ligand %d: rotatable bond index %d", i, e);
@@ -447,6 +481,23 @@ int dock_upload_ligands(dock_ctx* ctx, const dock_ligand_batch* b, int* batch_id
                 }
             }
             if (left[v]) return fail(ctx, DOCK_ERR_TOPOLOGY, "ligand %d: rotatable bond %d lies on a ring", i, e);
+            // refinement torsion: the side without atom 0 moves (side 1 = right fragment when atom 0 is left)
+            tor_depth.emplace_back(depth[left[0] ? v : u], r, left[0] ? 1 : 0);
+            {
+                std::vector<uint32_t> lw(wpr, 0u), rw(wpr, 0u);
+                for (int a = 0; a < l; ++a) {
+                    if (left[a] && a != u) lw[a >> 5] |= 1u << (a & 31);
+                    if (!left[a] && a != v) rw[a >> 5] |= 1u << (a & 31);
+                }
+                uint32_t* rows = check.data() + RL.check_off;
+                for (int a = 0; a < l; ++a) {
+                    const std::vector<uint32_t>* other = (lw[a >> 5] >> (a & 31)) & 1u   ? &rw
+                                                         : (rw[a >> 5] >> (a & 31)) & 1u ? &lw
+                                                                                          : nullptr;
+                    if (other)
+                        for (int w = 0; w < wpr; ++w) rows[(size_t)a * wpr + w] |= (*other)[w];
+                }
+            }
             for (int side = 0; side < 2; ++side) {
                 // side 0: the left fragment moves (c = u, b = v); side 1: the right one (c = v, b = u)
                 int c = side == 0 ? u : v, bb = side == 0 ? v : u;
@@ -478,6 +529,12 @@ int dock_upload_ligands(dock_ctx* ctx, const dock_ligand_batch* b, int* batch_id
                 B.side_nfixB.push_back(l - m - 1);
             }
         }
+        // deepest bond first, ties in bond order
+        std::stable_sort(tor_depth.begin(), tor_depth.end(),
+                         [](const std::tuple<int, int, int>& a, const std::tuple<int, int, int>& c) {
+                             return std::get<0>(a) > std::get<0>(c);
+                         });
+        for (const auto& td : tor_depth) rtor.push_back({2 * std::get<1>(td) + std::get<2>(td), std::get<1>(td)});
     }
     B.natoms = b->n > 0 ? b->atom_off[b->n] : 0;
     B.nside_total = (int)sides.size();
@@ -493,6 +550,15 @@ int dock_upload_ligands(dock_ctx* ctx, const dock_ligand_batch* b, int* batch_id
     if (!sides.empty()) CK(cudaMemcpy(B.side->p, sides.data(), sides.size() * sizeof(SideDev), cudaMemcpyHostToDevice));
     if (!idx.empty()) CK(cudaMemcpy(B.idx->p, idx.data(), idx.size(), cudaMemcpyHostToDevice));
     if (B.natoms) CK(cudaMemcpy(B.xyz0->p, b->xyz, (size_t)B.natoms * 3 * sizeof(float), cudaMemcpyHostToDevice));
+    B.rlig.reset(new DevBuf());
+    B.rtor.reset(new DevBuf());
+    B.check.reset(new DevBuf());
+    CK(B.rlig->ensure(std::max<size_t>(1, rlig.size()) * sizeof(RefLigDev)));
+    CK(B.rtor->ensure(std::max<size_t>(1, rtor.size()) * sizeof(RefTorDev)));
+    CK(B.check->ensure(std::max<size_t>(1, check.size()) * sizeof(uint32_t)));
+    if (!rlig.empty()) CK(cudaMemcpy(B.rlig->p, rlig.data(), rlig.size() * sizeof(RefLigDev), cudaMemcpyHostToDevice));
+    if (!rtor.empty()) CK(cudaMemcpy(B.rtor->p, rtor.data(), rtor.size() * sizeof(RefTorDev), cudaMemcpyHostToDevice));
+    if (!check.empty()) CK(cudaMemcpy(B.check->p, check.data(), check.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
     B.live = true;
     ctx->batches.push_back(std::move(B));
     *batch_id = (int)ctx->batches.size() - 1;
@@ -1116,3 +1182,243 @@ extern "C" int dock_run_static(dock_ctx* ctx, int batch_id, int pocket_id, const
     }
     return DOCK_OK;
 }
+
+// ------------------------------------------------------------ local refinement
+
+namespace {
+
+int check_batch(dock_ctx* ctx, int batch_id) {
+    if (!ctx) return DOCK_ERR_INVALID_ARG;
+    if (batch_id < 0 || batch_id >= (int)ctx->batches.size() || !ctx->batches[batch_id].live)
+        return fail(ctx, DOCK_ERR_INVALID_ARG, "bad batch id");
+    return DOCK_OK;
+}
+
+int check_pocket(dock_ctx* ctx, int pocket_id) {
+    if (pocket_id < 0 || pocket_id >= (int)ctx->pockets.size() || !ctx->pockets[pocket_id].live)
+        return fail(ctx, DOCK_ERR_INVALID_ARG, "bad pocket id %d", pocket_id);
+    return DOCK_OK;
+}
+
+ScoreParams score_params(dock_ctx* ctx, const BatchH& B, const PocketDev* pocket_dev) {
+    (void)ctx;
+    ScoreParams P{};
+    P.lig = B.lig->as<LigDev>();
+    P.side = B.side->as<SideDev>();
+    P.idx = B.idx->as<uint8_t>();
+    P.rlig = B.rlig->as<RefLigDev>();
+    P.rtor = B.rtor->as<RefTorDev>();
+    P.pocket = pocket_dev;
+    P.nlig = B.n;
+    return P;
+}
+
+// Device descriptor of one pocket (written once at dock_init_pocket).
+int pocket_on_device(dock_ctx* ctx, int pocket_id, cudaStream_t s, const PocketDev** out) {
+    (void)s;
+    *out = ctx->pockets[pocket_id].dev->as<PocketDev>();
+    return DOCK_OK;
+}
+
+// Device array of the descriptors of a pocket list, built once per list.
+int pocket_set(dock_ctx* ctx, const int32_t* pids, int np, const PocketDev** out) {
+    std::string key;
+    for (int i = 0; i < np; ++i) key += std::to_string(pids[i]) + ",";
+    auto it = ctx->pocket_sets.find(key);
+    if (it == ctx->pocket_sets.end()) {
+        std::vector<PocketDev> pd(np);
+        for (int i = 0; i < np; ++i) pd[i] = ctx->pockets[pids[i]].d;
+        std::unique_ptr<DevBuf> buf(new DevBuf());
+        CK(buf->ensure(np * sizeof(PocketDev)));
+        CK(cudaMemcpy(buf->p, pd.data(), np * sizeof(PocketDev), cudaMemcpyHostToDevice));
+        it = ctx->pocket_sets.emplace(key, std::move(buf)).first;
+    }
+    *out = it->second->as<PocketDev>();
+    return DOCK_OK;
+}
+
+int refine_impl(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const dock_knobs* k, const float* xyz_in,
+                dock_result* out, float* xyz_out, int on_device, const dock_refine_trace_buf* tr, cudaStream_t s) {
+    int rc = check_run_args(ctx, batch_id, pids, np, k);
+    if (rc) return rc;
+    if (!xyz_in || !out || !xyz_out) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_refine: NULL buffer");
+    CK(cudaSetDevice(ctx->device));
+    const BatchH& B = ctx->batches[batch_id];
+    const int npairs = np * B.n;
+    const size_t xbytes = (size_t)np * B.natoms * 3 * sizeof(float);
+    const PocketDev* pset = nullptr;
+    if ((rc = pocket_set(ctx, pids, np, &pset))) return rc;
+    const float* xin = xyz_in;
+    float* xout = xyz_out;
+    float* res = reinterpret_cast<float*>(out);
+    if (!on_device) {
+        CK(ctx->ref_xyz_in.ensure(std::max<size_t>(xbytes, 16)));
+        CK(ctx->ref_xyz_out.ensure(std::max<size_t>(xbytes, 16)));
+        CK(ctx->ref_res.ensure(std::max<size_t>((size_t)npairs * sizeof(dock_result), 16)));
+        if (xbytes) CK(cudaMemcpyAsync(ctx->ref_xyz_in.p, xyz_in, xbytes, cudaMemcpyHostToDevice, s));
+        xin = ctx->ref_xyz_in.as<float>();
+        xout = ctx->ref_xyz_out.as<float>();
+        res = ctx->ref_res.as<float>();
+    }
+    RefineParams P{};
+    P.lig = B.lig->as<LigDev>();
+    P.side = B.side->as<SideDev>();
+    P.idx = B.idx->as<uint8_t>();
+    P.rlig = B.rlig->as<RefLigDev>();
+    P.rtor = B.rtor->as<RefTorDev>();
+    P.check = B.check->as<uint32_t>();
+    P.pockets = pset;
+    P.npairs = npairs;
+    P.nlig = B.n;
+    P.natoms = B.natoms;
+    P.steps = k->refine_steps;
+    P.clip = k->clip_box;
+    P.thr2 = (float)(k->bump_thr * k->bump_thr);
+    P.xyz_in = xin;
+    P.xyz_out = xout;
+    P.result = res;
+    std::vector<DevBuf> tbuf(10);
+    const int ns = npairs * k->refine_steps;
+    if (tr) {
+        if (tr->gstride < 6 + B.tmax) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_refine_trace: gstride too small");
+        P.trace_on = 1;
+        P.tr.gstride = tr->gstride;
+        size_t sz[10] = {(size_t)ns * tr->gstride * 4, (size_t)ns * 4, (size_t)ns * 4, (size_t)ns * 4, (size_t)ns * 4,
+                         (size_t)ns * 4, (size_t)npairs * 4, (size_t)npairs * 4, (size_t)npairs * 4, 0};
+        for (int i = 0; i < 9; ++i) {
+            CK(tbuf[i].ensure(std::max<size_t>(sz[i], 16)));
+            CK(cudaMemsetAsync(tbuf[i].p, 0, std::max<size_t>(sz[i], 16), s));
+        }
+        P.tr.G = tbuf[0].as<float>();
+        P.tr.D = tbuf[1].as<float>();
+        P.tr.lam = tbuf[2].as<float>();
+        P.tr.S_new = tbuf[3].as<float>();
+        P.tr.verdict = tbuf[4].as<int32_t>();
+        P.tr.accept = tbuf[5].as<int32_t>();
+        P.tr.S_start = tbuf[6].as<float>();
+        P.tr.S_final = tbuf[7].as<float>();
+        P.tr.status = tbuf[8].as<int32_t>();
+    }
+    CK(launch_refine(P, B.lmax, B.tmax, s));
+    if (tr) {
+        CK(cudaStreamSynchronize(s));
+        CK(cudaMemcpy(tr->G, P.tr.G, (size_t)ns * tr->gstride * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(tr->D, P.tr.D, (size_t)ns * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(tr->lam, P.tr.lam, (size_t)ns * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(tr->S_new, P.tr.S_new, (size_t)ns * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(tr->verdict, P.tr.verdict, (size_t)ns * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(tr->accept, P.tr.accept, (size_t)ns * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(tr->S_start, P.tr.S_start, (size_t)npairs * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(tr->S_final, P.tr.S_final, (size_t)npairs * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(tr->status, P.tr.status, (size_t)npairs * 4, cudaMemcpyDeviceToHost));
+    }
+    if (!on_device) {
+        if (npairs) CK(cudaMemcpyAsync(out, res, (size_t)npairs * sizeof(dock_result), cudaMemcpyDeviceToHost, s));
+        if (xbytes) CK(cudaMemcpyAsync(xyz_out, xout, xbytes, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return DOCK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dock_batch_info(dock_ctx* ctx, int batch_id, int* n, int* natoms, int* lmax, int* tmax) {
+    int rc = check_batch(ctx, batch_id);
+    if (rc) return rc;
+    const BatchH& B = ctx->batches[batch_id];
+    if (n) *n = B.n;
+    if (natoms) *natoms = B.natoms;
+    if (lmax) *lmax = B.lmax;
+    if (tmax) *tmax = B.tmax;
+    return DOCK_OK;
+}
+
+int dock_score_trilinear(dock_ctx* ctx, int batch_id, int pocket_id, int clip, const float* xyz, float* o,
+                         void* stream) {
+    int rc = check_batch(ctx, batch_id);
+    if (rc || (rc = check_pocket(ctx, pocket_id))) return rc;
+    if (!xyz || !o) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_score_trilinear: NULL buffer");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const PocketDev* pdev = nullptr;
+    if ((rc = pocket_on_device(ctx, pocket_id, s, &pdev))) return rc;
+    const BatchH& B = ctx->batches[batch_id];
+    ScoreParams P = score_params(ctx, B, pdev);
+    P.clip = clip != 0;
+    P.x = xyz;
+    P.out = o;
+    CK(launch_score(P, B.lmax, SCORE_FWD, s));
+    return DOCK_OK;
+}
+
+int dock_score_trilinear_grad(dock_ctx* ctx, int batch_id, int pocket_id, int clip, const float* xyz,
+                              const float* grad_o, float* grad_xyz, void* stream) {
+    int rc = check_batch(ctx, batch_id);
+    if (rc || (rc = check_pocket(ctx, pocket_id))) return rc;
+    if (!xyz || !grad_xyz) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_score_trilinear_grad: NULL buffer");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const PocketDev* pdev = nullptr;
+    if ((rc = pocket_on_device(ctx, pocket_id, s, &pdev))) return rc;
+    const BatchH& B = ctx->batches[batch_id];
+    ScoreParams P = score_params(ctx, B, pdev);
+    P.clip = clip != 0;
+    P.x = xyz;
+    P.grad_in = grad_o;
+    P.out = grad_xyz;
+    CK(launch_score(P, B.lmax, SCORE_BWD, s));
+    return DOCK_OK;
+}
+
+int dock_dof_apply(dock_ctx* ctx, int batch_id, const float* x, const float* q, int qstride, float* z, void* stream) {
+    int rc = check_batch(ctx, batch_id);
+    if (rc) return rc;
+    const BatchH& B = ctx->batches[batch_id];
+    if (!x || !q || !z) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_dof_apply: NULL buffer");
+    if (qstride < 6 + B.tmax) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_dof_apply: qstride < 6 + tmax");
+    CK(cudaSetDevice(ctx->device));
+    ScoreParams P = score_params(ctx, B, nullptr);
+    P.x = x;
+    P.q = q;
+    P.qstride = qstride;
+    P.out = z;
+    CK(launch_score(P, B.lmax, DOF_APPLY, (cudaStream_t)stream));
+    return DOCK_OK;
+}
+
+int dock_dof_grad(dock_ctx* ctx, int batch_id, const float* x, const float* q, int qstride, const float* grad_z,
+                  float* grad_q, void* stream) {
+    int rc = check_batch(ctx, batch_id);
+    if (rc) return rc;
+    const BatchH& B = ctx->batches[batch_id];
+    if (!x || !q || !grad_z || !grad_q) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_dof_grad: NULL buffer");
+    if (qstride < 6 + B.tmax) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_dof_grad: qstride < 6 + tmax");
+    CK(cudaSetDevice(ctx->device));
+    ScoreParams P = score_params(ctx, B, nullptr);
+    P.x = x;
+    P.q = q;
+    P.qstride = qstride;
+    P.grad_in = grad_z;
+    P.out = grad_q;
+    CK(launch_score(P, B.lmax, DOF_GRAD, (cudaStream_t)stream));
+    return DOCK_OK;
+}
+
+int dock_refine(dock_ctx* ctx, int batch_id, const int32_t* pocket_ids, int npockets, const dock_knobs* k,
+                const float* xyz_in, dock_result* out, float* xyz_out, int on_device, void* stream) {
+    return refine_impl(ctx, batch_id, pocket_ids, npockets, k, xyz_in, out, xyz_out, on_device, nullptr,
+                       (cudaStream_t)stream);
+}
+
+int dock_refine_trace(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs* k, const float* xyz_in,
+                      const dock_refine_trace_buf* tr, dock_result* out, float* xyz_out) {
+    if (!tr || !tr->G || !tr->D || !tr->lam || !tr->S_new || !tr->verdict || !tr->accept || !tr->S_start ||
+        !tr->S_final || !tr->status)
+        return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_refine_trace: NULL trace buffer");
+    int32_t pid = pocket_id;
+    return refine_impl(ctx, batch_id, &pid, 1, k, xyz_in, out, xyz_out, 0, tr, nullptr);
+}
+
+}  // extern "C"

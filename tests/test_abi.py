@@ -45,3 +45,13 @@ def test_host_only_calls_without_gpu(lib):
     # no context: calls fail with an error code instead of crashing
     assert g.lib.dock_run(None, 0, None, 0, None, None, None, 0, None) == g.DOCK_ERR_INVALID_ARG
     assert g.lib.dock_last_error(None) == b"no context"
+
+
+def test_refinement_calls_fail_cleanly_without_context(lib):
+    import paper_1901_06363_gb300 as g
+    assert g.lib.dock_batch_info(None, 0, None, None, None, None) == g.DOCK_ERR_INVALID_ARG
+    assert g.lib.dock_score_trilinear(None, 0, 0, 1, None, None, None) == g.DOCK_ERR_INVALID_ARG
+    assert g.lib.dock_dof_apply(None, 0, None, None, 6, None, None) == g.DOCK_ERR_INVALID_ARG
+    assert g.lib.dock_dof_grad(None, 0, None, None, 6, None, None, None) == g.DOCK_ERR_INVALID_ARG
+    assert g.lib.dock_refine(None, 0, None, 0, None, None, None, None, 0, None) == g.DOCK_ERR_INVALID_ARG
+    assert g.lib.dock_refine_trace(None, 0, 0, None, None, None, None, None) == g.DOCK_ERR_INVALID_ARG
