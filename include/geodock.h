@@ -116,7 +116,11 @@ typedef struct {
  *                      squared distance outside it
  *   bump_thr           Å; a candidate is infeasible when an atom pair whose
  *                      distance depends on the torsion is closer than this
- *   score_mode         0 nearest voxel, 1 trilinear interpolation of K
+ *   score_mode         0 nearest voxel, 1 trilinear interpolation of K,
+ *                      2 exact: Eq. 1's inner minimum over the pocket's
+ *                      probe points themselves, O(l p) per candidate (the
+ *                      paper's own cost profile; needs the pocket's pts;
+ *                      runs with 12 angles per chunk)
  *   refine_steps       ascent steps of dock_refine (0..1000); dock_run ignores it
  *   seed               seed of the initial orientations
  *   plain_mode         1: one launch per (pocket, ligand) pair, no bucketing

@@ -55,6 +55,7 @@ struct PocketH {
     PocketDev d{};
     std::unique_ptr<DevBuf> K, Kp;
     std::unique_ptr<DevBuf> dev;  // device copy of d
+    std::unique_ptr<DevBuf> pts;  // probe points for the exact score (float4, voxel + 0.5)
 };
 
 struct BatchH {
@@ -171,7 +172,7 @@ int check_knobs(dock_ctx* ctx, const dock_knobs* k) {
     if (k->n_poses < 1 || k->n_poses > DOCK_MAX_POSES) return fail(ctx, DOCK_ERR_INVALID_ARG, "knobs: n_poses");
     if (!(k->bump_thr >= 0.0) || !std::isfinite(k->bump_thr)) return fail(ctx, DOCK_ERR_INVALID_ARG, "knobs: bump_thr");
     if (!std::isfinite(k->threshold)) return fail(ctx, DOCK_ERR_INVALID_ARG, "knobs: threshold");
-    if (k->score_mode != 0 && k->score_mode != 1) return fail(ctx, DOCK_ERR_INVALID_ARG, "knobs: score_mode");
+    if (k->score_mode < 0 || k->score_mode > 2) return fail(ctx, DOCK_ERR_INVALID_ARG, "knobs: score_mode");
     if (k->refine_steps < 0 || k->refine_steps > 1000) return fail(ctx, DOCK_ERR_INVALID_ARG, "knobs: refine_steps");
     if (k->enable_refinement && peel_tile(k->hp_step) < 0)
         return fail(ctx, DOCK_ERR_UNSUPPORTED, "knobs: no tile size divides 360 for this step");
@@ -198,6 +199,10 @@ dock_tile default_tile(const dock_knobs* k) {
     int ncand = n_angles(k->hp_step) - 1;
     t.angles_per_chunk = ncand <= 8 ? 8 : (ncand <= 12 ? 12 : (ncand <= 18 ? 18 : 36));
     t.warps_per_cta = t.angles_per_chunk == 36 ? 8 : 4;
+    if (k->score_mode == 2) {
+        t.angles_per_chunk = 12;  // the only instantiation of the exact score
+        t.warps_per_cta = 4;
+    }
     return t;
 }
 
@@ -359,6 +364,21 @@ int dock_init_pocket(dock_ctx* ctx, const dock_pocket* p, int* pocket_id) {
                                                                 p->ny, p->nz);
         CK(cudaGetLastError());
         CK(cudaDeviceSynchronize());
+    }
+    // probe points for the exact score (Eq. 1's inner minimum without the grid)
+    if (p->pts && p->npts > 0) {
+        std::vector<float4> q(p->npts);
+        for (int j = 0; j < p->npts; ++j) {
+            int x = p->pts[3 * j], y = p->pts[3 * j + 1], z = p->pts[3 * j + 2];
+            if (x < 0 || y < 0 || z < 0 || x >= p->nx || y >= p->ny || z >= p->nz)
+                return fail(ctx, DOCK_ERR_INVALID_ARG, "pocket: probe point %d outside the grid", j);
+            q[j] = make_float4(x + 0.5f, y + 0.5f, z + 0.5f, 0.f);
+        }
+        ph.pts.reset(new DevBuf());
+        CK(ph.pts->ensure(q.size() * sizeof(float4)));
+        CK(cudaMemcpy(ph.pts->p, q.data(), q.size() * sizeof(float4), cudaMemcpyHostToDevice));
+        ph.d.pts = ph.pts->as<float4>();
+        ph.d.npts = p->npts;
     }
     ph.d.K = ph.K->as<uint16_t>();
     ph.d.Kp = ph.Kp->as<uint32_t>();
@@ -625,6 +645,7 @@ dock_tile resolve_tile(dock_ctx* ctx, int batch_id, const dock_knobs* k) {
     if (ctx->tile.lanes_per_pose) t.lanes_per_pose = ctx->tile.lanes_per_pose;
     if (ctx->tile.angles_per_chunk) t.angles_per_chunk = ctx->tile.angles_per_chunk;
     if (ctx->tile.warps_per_cta) t.warps_per_cta = ctx->tile.warps_per_cta;
+    if (k->score_mode == 2) t.angles_per_chunk = 12;
     return t;
 }
 
@@ -765,7 +786,7 @@ int get_plan(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const doc
     F.nlig = B.n;
     F.natoms = B.natoms;
     F.n_poses = N;
-    F.shift = k->score_mode == 0 ? 0.5f : 0.0f;
+    F.shift = k->score_mode == 1 ? 0.0f : 0.5f;
     F.score = ctx->res.as<float>();
     F.xyz_out = ctx->xyz_res.as<float>();
     *out = pl.get();
@@ -819,6 +840,10 @@ int check_run_args(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, con
             return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_run: bad pocket id %d", pids[i]);
     int rc = check_knobs(ctx, k);
     if (rc) return rc;
+    if (k->score_mode == 2)
+        for (int i = 0; i < np; ++i)
+            if (ctx->pockets[pids[i]].d.npts < 1)
+                return fail(ctx, DOCK_ERR_UNSUPPORTED, "exact score: pocket %d was given without probe points", pids[i]);
     int64_t pairs = (int64_t)np * ctx->batches[batch_id].n;
     if (pairs * k->n_poses > (int64_t)1 << 31) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_run: too many poses");
     return DOCK_OK;
@@ -961,7 +986,8 @@ int dock_autotune(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs* 
     std::vector<int> Qs;
     for (int q : {1, 2, 4, 8})
         if (32 / q <= 2 * k->n_poses || q == 8) Qs.push_back(q);
-    const int kcs[4] = {8, 12, 18, 36};
+    std::vector<int> kcs{8, 12, 18, 36};
+    if (k->score_mode == 2) kcs = {12};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1098,6 +1124,7 @@ extern "C" int dock_run_static(dock_ctx* ctx, int batch_id, int pocket_id, const
     if (ctx->tile.lanes_per_pose) t.lanes_per_pose = ctx->tile.lanes_per_pose;
     if (ctx->tile.angles_per_chunk) t.angles_per_chunk = ctx->tile.angles_per_chunk;
     if (ctx->tile.warps_per_cta) t.warps_per_cta = ctx->tile.warps_per_cta;
+    if (k->score_mode == 2) t.angles_per_chunk = 12;
     const int slice = slice_floats(t, B.lmax);
     const int lq = lanes_log2(t, slice, B.lmax);  // sized for the largest ligand
     const int G = 32 >> lq, W = t.warps_per_cta, block = 32 * W;
@@ -1174,7 +1201,7 @@ extern "C" int dock_run_static(dock_ctx* ctx, int batch_id, int pocket_id, const
         F.nlig = B.n;
         F.natoms = B.natoms;
         F.n_poses = N;
-        F.shift = k->score_mode == 0 ? 0.5f : 0.0f;
+        F.shift = k->score_mode == 1 ? 0.0f : 0.5f;
         F.score = reinterpret_cast<float*>(out);
         F.xyz_out = xyz_out;
         finalize_kernel<<<(B.n + 3) / 4, 128, 0, s>>>(F);

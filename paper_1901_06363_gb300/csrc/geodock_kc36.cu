@@ -12,6 +12,7 @@ static cudaError_t go(const SweepParams& P, int grid, int block, size_t smem, cu
 
 cudaError_t launch_sweep_kc36(const SweepParams& P, int mode, int clip, int grid, int block, size_t smem,
                                cudaStream_t s) {
+    if (mode == 2) return cudaErrorInvalidValue;  // the exact score runs with 12 angles per chunk only
     if (mode == 0) return clip ? go<0, true>(P, grid, block, smem, s) : go<0, false>(P, grid, block, smem, s);
     return clip ? go<1, true>(P, grid, block, smem, s) : go<1, false>(P, grid, block, smem, s);
 }
@@ -33,6 +34,7 @@ static cudaError_t occ(int block, size_t smem, int* n) {
 }
 
 cudaError_t occupancy_kc36(int mode, int clip, int block, size_t smem, int* n) {
+    if (mode == 2) return cudaErrorInvalidValue;
     if (mode == 0) return clip ? occ<0, true>(block, smem, n) : occ<0, false>(block, smem, n);
     return clip ? occ<1, true>(block, smem, n) : occ<1, false>(block, smem, n);
 }

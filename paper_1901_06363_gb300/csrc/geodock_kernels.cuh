@@ -17,7 +17,8 @@
 //
 // Score (Eq. 1): o = l / (h^2 S), S = sum_i K(voxel(x_i)) in grid units with K
 // the floored integer field, so S is an exact integer (nearest mode) and the
-// argmax is an exact integer comparison. Trilinear mode interpolates K.
+// argmax is an exact integer comparison. Trilinear mode interpolates K; the
+// exact mode takes Eq. 1's inner minimum over the pocket points directly.
 //
 // Bump check (Alg. 1 "the ligand shape is feasible"): pairs (i in M\{c},
 // j in F\{b}). For atom i on its circle (centre a, radius r = |u|) and a fixed
@@ -43,6 +44,8 @@ constexpr uint32_t OUTSIDE = 1u << 24;
 struct PocketDev {
     const uint16_t* K;   // floored field, x fastest
     const uint32_t* Kp;  // the same values padded by PAD voxels per side, OUTSIDE beyond the grid
+    const float4* pts;   // probe points (voxel index + 0.5, grid units) for the exact score; NULL if unknown
+    int npts;
     int nx, ny, nz;
     double h;  // voxel edge (Å)
     double origin[3];
@@ -164,15 +167,32 @@ __device__ __forceinline__ float3 place(const Split& s, float cs, float sn) {
                        __fmaf_rn(sn, s.w.z, __fmaf_rn(cs, s.u.z, s.a.z)));
 }
 
+// Eq. 1's inner minimum taken over the probe points themselves, at grid
+// position t shifted by +0.5 (points stored shifted alike), floored at 1.
+__device__ __forceinline__ float exact_min(const PocketDev& pd, float3 t) {
+    float m = 3.0e38f;
+    for (int j = 0; j < pd.npts; ++j) {
+        const float4 q = __ldg(pd.pts + j);
+        const float dx = t.x - q.x, dy = t.y - q.y, dz = t.z - q.z;
+        m = fminf(m, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    }
+    return fmaxf(m, 1.f);
+}
+
 // Field term of one atom at shifted grid position t.
 // MODE 0 nearest (t shifted by +0.5: voxel = floor(t), inside iff 0 <= t < n)
 // MODE 1 trilinear (unshifted: inside iff 0 <= t <= n-1)
+// MODE 2 exact points (shifted as MODE 0, same inside test; no outside penalty:
+//        the distance to the points is defined everywhere)
 // Returns the term; *in reports whether the atom is inside the box. With
 // CLIP the value is only meaningful when inside; without CLIP the lookup is
 // clamped and the squared excess outside the box is added.
 template <int MODE, bool CLIP>
 __device__ __forceinline__ float term(const PocketDev& pd, const uint16_t* __restrict__ K, float3 t, bool* in) {
-    if (MODE == 0) {
+    if (MODE == 2) {
+        *in = (vox(t.x) < (uint32_t)pd.nx) & (vox(t.y) < (uint32_t)pd.ny) & (vox(t.z) < (uint32_t)pd.nz);
+        return exact_min(pd, t);
+    } else if (MODE == 0) {
         uint32_t ix = vox(t.x), iy = vox(t.y), iz = vox(t.z);
         bool inside = (ix < (uint32_t)pd.nx) & (iy < (uint32_t)pd.ny) & (iz < (uint32_t)pd.nz);
         *in = inside;
@@ -297,6 +317,10 @@ template <>
 struct Acc<1> {
     using T = float;
 };
+template <>
+struct Acc<2> {
+    using T = float;
+};
 
 // Value of the padded field at padded shifted position t (nearest mode), for
 // a position known to lie inside the padded box: floor by the
@@ -367,6 +391,33 @@ __device__ __forceinline__ void score_atoms(const PocketDev& pd, const uint16_t*
                 }
             }
         }
+    } else if (MODE == 2) {
+        // exact points: the chunk's positions stay in registers while the points stream by
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            float3 t[KC];
+            float m[KC];
+#pragma unroll
+            for (int j = 0; j < KC; ++j) {
+                t[j] = place(s[a], cst[j].x, cst[j].y);
+                m[j] = 3.0e38f;
+            }
+            for (int p = 0; p < pd.npts; ++p) {
+                const float4 q = __ldg(pd.pts + p);
+#pragma unroll
+                for (int j = 0; j < KC; ++j) {
+                    const float dx = t[j].x - q.x, dy = t[j].y - q.y, dz = t[j].z - q.z;
+                    m[j] = fminf(m[j], fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < KC; ++j) {
+                acc[j] += fmaxf(m[j], 1.f);
+                const bool in = (vox(t[j].x) < (uint32_t)pd.nx) & (vox(t[j].y) < (uint32_t)pd.ny) &
+                                (vox(t[j].z) < (uint32_t)pd.nz);
+                if (CLIP && !in) box |= 1ull << j;
+            }
+        }
     } else {
 #pragma unroll
         for (int j = 0; j < KC; ++j) {
@@ -392,7 +443,7 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
     float2* ptab = reinterpret_cast<float2*>(xs + P.slice + P.bw * 64);             // the phase's (cos, sin)
     uint8_t* sidx = reinterpret_cast<uint8_t*>(ptab + 64 * P.bw + KC);              // the sweep's index lists
     unsigned long long* col = bump + lane;
-    const float shift = MODE == 0 ? 0.5f : 0.0f;
+    const float shift = MODE == 1 ? 0.0f : 0.5f;
 
     for (;;) {
         int task = 0;

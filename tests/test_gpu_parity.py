@@ -101,9 +101,9 @@ def test_tile_shapes_bit_identical(dk):
 
 
 @pytest.mark.parametrize("variant", ["threshold", "noclip", "peel", "trilinear", "trilinear_noclip", "reps0",
-                                     "step360"])
+                                     "step360", "exact", "exact_noclip", "exact_peel"])
 def test_knob_variants(dk, variant):
-    n_grid = 40 if variant == "noclip" or variant == "trilinear_noclip" else 64
+    n_grid = 40 if variant in ("noclip", "trilinear_noclip", "exact_noclip") else 64
     pk = synth.pocket(13, n_grid, 0.5, (6, 5, 4))
     l, t = synth.ligand_sizes(13, 8, 0, [16, 48, 2, 8])
     b = synth.ligand_batch(13, l, t)
@@ -116,6 +116,9 @@ def test_knob_variants(dk, variant):
         "trilinear_noclip": dict(score_mode=1, clip_box=0),
         "reps0": dict(repetitions=0),
         "step360": dict(hp_step=360.0, lp_step=360.0),
+        "exact": dict(score_mode=2),
+        "exact_noclip": dict(score_mode=2, clip_box=0),
+        "exact_peel": dict(score_mode=2, enable_refinement=1, hp_step=5.0, lp_step=30.0, threshold=0.3),
     }[variant])
     trace_parity(dk, pk, b, kn)
 
@@ -196,4 +199,23 @@ def test_bench_workload_sampled(dk):
     opk = oracle.OraclePocket(pks[0])
     _, g, res_sub = trace_parity(dk, pks[0], sub, kn, opk=opk, ids=sample)
     assert np.array_equal(res_sub.view(np.int32), res[sample].view(np.int32))
+    dk.release_batch(bid)
+
+
+def test_exact_score_needs_probe_points(dk):
+    from paper_1901_06363_gb300 import DOCK_ERR_UNSUPPORTED, DockError
+    pk = synth.pocket(14, 48, 0.5, C.ELLIPSOID)
+    K = oracle.field(pk.dims, pk.pts)
+    bare = synth.Pocket(pk.dims, pk.h, pk.origin, pk.centre, np.zeros((0, 3), np.int32))
+    pid = dk.init_pocket(bare, K=K)
+    b = synth.ligand_batch(3, np.array([12]), np.array([2]))
+    bid = dk.upload_ligands(b)
+    with pytest.raises(DockError) as ei:
+        dk.run(bid, [pid], C.knobs(score_mode=2), b.n, _natoms(b))
+    assert ei.value.code == DOCK_ERR_UNSUPPORTED
+    # the same pocket with its points gives the exact score, and nearest mode is unaffected by them
+    pid2 = dk.init_pocket(pk)
+    r0, _ = dk.run(bid, [pid], C.knobs(), b.n, _natoms(b))
+    r1, _ = dk.run(bid, [pid2], C.knobs(), b.n, _natoms(b))
+    assert np.array_equal(r0.view(np.int32), r1.view(np.int32))
     dk.release_batch(bid)
