@@ -1,0 +1,81 @@
+"""The knob-sweep and multi-pocket workloads on the GPU: full-size (or large-sample) runs checked by
+properties, and sampled ligands replayed against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import parity
+import synth
+import synth.configs as C
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dk():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_06363_gb300 import Docker
+    d = Docker(0)
+    yield d
+    d.close()
+
+
+def _replay_sample(dk, pk, pid, batch, kn, sample, grouped_res):
+    """Trace the sampled ligands alone (same ids), replay them in the oracle, and compare with the batch run."""
+    sub = batch.subset(sample)
+    bid = dk.upload_ligands(sub, ids=sample + batch.id_base)
+    g = dk.run_trace(bid, pid, kn, sub)
+    orc = parity.replay(oracle.OraclePocket(pk), sub, kn, g, ids=sample + batch.id_base)
+    stats = parity.check(sub, kn, g, orc)
+    parity.check_best(sub, kn, g["result"], g["pose_S"], g["pose_status"])
+    assert np.array_equal(g["result"].view(np.int32), grouped_res.view(np.int32))
+    dk.release_batch(bid)
+    return stats
+
+
+def test_multi_pocket_grouped_launch(dk):
+    """16 pockets (48^3-128^3) x 50,000 lognormal ligands in one grouped launch; 32 poses, 15 degrees, 2 reps."""
+    pks, b, kn = C.multi_pocket()
+    pids = [dk.init_pocket(pk) for pk in pks]
+    bid = dk.upload_ligands(b)
+    natoms = int(b.atom_off[-1])
+    res, _ = dk.run(bid, pids, kn, b.n, natoms, xyz=False)
+    res = res.reshape(len(pks), b.n)
+    ok = res["status"] == 0
+    assert np.all(res["score"][ok] > 0) and np.all(res["score"][~ok] == 0)
+    assert np.all((res["pose"][ok] >= 0) & (res["pose"][ok] < kn["n_poses"])) and np.all(res["pose"][~ok] == -1)
+    assert ok.mean() > 0.9
+    dk.release_batch(bid)
+    # sampled ligands of every pocket replayed against the oracle; the grouped launch equals the single-pocket one
+    rng = np.random.default_rng(5)
+    sample = np.sort(rng.choice(b.n, 2, replace=False))
+    for i, (pk, pid) in enumerate(zip(pks, pids)):
+        _replay_sample(dk, pk, pid, b, kn, sample, res[i][sample])
+
+
+def test_knob_sweep_combinations(dk):
+    """The 45 (step, poses, repetitions) combinations on 2,048 lognormal ligands; sampled ligands replayed."""
+    pks, _, combos = C.knob_sweep(n=1)
+    b = C.sweep_batch(2048)
+    pid = dk.init_pocket(pks[0])
+    bid = dk.upload_ligands(b)
+    natoms = int(b.atom_off[-1])
+    best = {}
+    for kn in combos:
+        res, _ = dk.run(bid, [pid], kn, b.n, natoms, xyz=False)
+        ok = res["status"] == 0
+        assert ok.mean() > 0.9 and np.all(res["score"][ok] > 0)
+        best[(kn["hp_step"], kn["n_poses"], kn["repetitions"])] = res
+    # more poses or more repetitions never make a ligand's result worse on average
+    for s in C.SWEEP_STEPS:
+        m = [np.mean(best[(s, p, 4)]["score"]) for p in C.SWEEP_POSES]
+        assert m[0] <= m[1] <= m[2]
+        m = [np.mean(best[(s, 32, r)]["score"]) for r in C.SWEEP_REPS]
+        assert m[0] <= m[1] * (1 + 1e-6) and m[1] <= m[2] * (1 + 1e-6)
+    sample = np.array([3, 1500])
+    for (s, p, r) in [(5.0, 8, 1), (45.0, 128, 1), (20.0, 32, 4), (10.0, 8, 16)]:
+        kn = [k for k in combos if (k["hp_step"], k["n_poses"], k["repetitions"]) == (s, p, r)][0]
+        _replay_sample(dk, pks[0], pid, b, kn, sample, best[(s, p, r)][sample])
+    dk.release_batch(bid)
