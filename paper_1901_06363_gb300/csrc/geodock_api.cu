@@ -188,17 +188,19 @@ int trace_pmax(const dock_knobs* k) {
     return p;
 }
 
-// Default tile shape. lanes_per_pose applies to ligands of up to 32 atoms
-// (larger ligands double it per doubling of size, see lanes_log2): chosen so a
-// warp holds no more poses than the run has. angles_per_chunk covers a hp
-// sweep in few chunks.
+// Default tile shape. Two lanes share a pose (splitting its atoms) when the run
+// has at least 16 poses, more for fewer poses, so that a warp holds no more
+// poses than the run has; larger ligands get more lanes per pose (see
+// lanes_log2). Up to 18 angles per chunk keep a thread within 128 registers,
+// so two CTAs of 8 warps fit an SM; with one moving atom per pass the hot
+// code stays small enough for the instruction cache at that occupancy.
 dock_tile default_tile(const dock_knobs* k) {
     dock_tile t;
     int N = k->n_poses;
-    t.lanes_per_pose = N >= 32 ? 1 : (N >= 16 ? 2 : (N >= 8 ? 4 : 8));
+    t.lanes_per_pose = N >= 16 ? 2 : (N >= 8 ? 4 : 8);
     int ncand = n_angles(k->hp_step) - 1;
-    t.angles_per_chunk = ncand <= 8 ? 8 : (ncand <= 12 ? 12 : (ncand <= 18 ? 18 : 36));
-    t.warps_per_cta = t.angles_per_chunk == 36 ? 8 : 4;
+    t.angles_per_chunk = ncand <= 8 ? 8 : (ncand <= 12 ? 12 : 18);
+    t.warps_per_cta = 8;
     if (k->score_mode == 2) {
         t.angles_per_chunk = 12;  // the only instantiation of the exact score
         t.warps_per_cta = 4;

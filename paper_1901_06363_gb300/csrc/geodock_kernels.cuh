@@ -360,7 +360,8 @@ __device__ __forceinline__ float outside2(const PocketDev& pd, float3 t) {
 template <int KC, int MODE, bool CLIP, int NA>
 __device__ __forceinline__ void score_atoms(const PocketDev& pd, const uint16_t* __restrict__ K, uint32_t bias,
                                             const Split (&s)[NA], bool fast, const float2* __restrict__ cst,
-                                            typename Acc<MODE>::T (&acc)[KC], float (&pen)[KC], uint64_t& box) {
+                                            typename Acc<MODE>::T (&acc)[KC], float (&pen)[KC], uint64_t& box,
+                                            uint64_t need) {
     if (MODE == 0 && fast) {
         // padded field: circle centres moved by PAD voxels; outside values sum past OUTSIDE
         Split sp[NA];
@@ -370,11 +371,18 @@ __device__ __forceinline__ void score_atoms(const PocketDev& pd, const uint16_t*
             sp[a].a = make_float3(s[a].a.x + (float)PAD, s[a].a.y + (float)PAD, s[a].a.z + (float)PAD);
         }
         const uint32_t pnx = (uint32_t)(pd.nx + 2 * PAD), pny = (uint32_t)(pd.ny + 2 * PAD);
+        // blocks of candidates that no pose of the warp needs (all infeasible) are skipped
+        constexpr int BLK = KC % 6 == 0 ? 6 : 4;
 #pragma unroll
-        for (int j = 0; j < KC; ++j) {
-            const float2 c = cst[j];
+        for (int jb = 0; jb < KC; jb += BLK) {
+            if ((need >> jb) & ((1ull << BLK) - 1ull)) {
 #pragma unroll
-            for (int a = 0; a < NA; ++a) acc[j] += lookup_padded(pd.Kp, pnx, pny, bias, place(sp[a], c.x, c.y));
+                for (int j = jb; j < jb + BLK && j < KC; ++j) {
+                    const float2 c = cst[j];
+#pragma unroll
+                    for (int a = 0; a < NA; ++a) acc[j] += lookup_padded(pd.Kp, pnx, pny, bias, place(sp[a], c.x, c.y));
+                }
+            }
         }
     } else if (MODE == 0) {
 #pragma unroll
@@ -473,17 +481,26 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
         const float hix = MODE == 0 ? nxf - lo : nxf - 1.f, hiy = MODE == 0 ? nyf - lo : nyf - 1.f,
                     hiz = MODE == 0 ? nzf - lo : nzf - 1.f;
 
-        // ---- initial rigid orientation (FP64), centroid on the pocket centre
+        // ---- initial rigid orientation, centroid on the pocket centre: the rotation (FP64) is
+        // scaled to grid units once per pose, the atoms are placed in FP32
         {
             double R[9];
             pose_matrix(P.seed, L.id, active ? p : 0, R);
+            const double ih = 1.0 / pd.h;
+            float M[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) M[k] = (float)(R[k] * ih);
+            const float ox = (float)((pd.centre[0] - pd.origin[0]) * ih + shift);
+            const float oy = (float)((pd.centre[1] - pd.origin[1]) * ih + shift);
+            const float oz = (float)((pd.centre[2] - pd.origin[2]) * ih + shift);
+            const float gx = (float)L.g[0], gy = (float)L.g[1], gz = (float)L.g[2];
             for (int i = q; i < L.l; i += Q) {
                 const float* x0 = P.xyz0 + 3 * (L.atom_off + i);
-                double d0 = (double)x0[0] - L.g[0], d1 = (double)x0[1] - L.g[1], d2 = (double)x0[2] - L.g[2];
+                const float d0 = x0[0] - gx, d1 = x0[1] - gy, d2 = x0[2] - gz;
                 float3 t;
-                t.x = (float)((pd.centre[0] + (R[0] * d0 + R[1] * d1 + R[2] * d2) - pd.origin[0]) / pd.h + shift);
-                t.y = (float)((pd.centre[1] + (R[3] * d0 + R[4] * d1 + R[5] * d2) - pd.origin[1]) / pd.h + shift);
-                t.z = (float)((pd.centre[2] + (R[6] * d0 + R[7] * d1 + R[8] * d2) - pd.origin[2]) / pd.h + shift);
+                t.x = fmaf(M[0], d0, fmaf(M[1], d1, fmaf(M[2], d2, ox)));
+                t.y = fmaf(M[3], d0, fmaf(M[4], d1, fmaf(M[5], d2, oy)));
+                t.z = fmaf(M[6], d0, fmaf(M[7], d1, fmaf(M[8], d2, oz)));
                 st3(xs, i, G, ps, t);
             }
         }
@@ -684,33 +701,33 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                                 pen[j] = 0.f;
                             }
                             uint64_t box = 0ull;
+                            // candidates of this chunk that some pose of the warp may still take
+                            uint64_t need;
+                            {
+                                const int w = j0 >> 6, sh = j0 & 63;
+                                uint64_t b0 = col[w * 32] >> sh;
+                                if (sh + KC > 64 && w + 1 < P.bw) b0 |= col[(w + 1) * 32] << (64 - sh);
+                                b0 = group_or(b0, Q);
+                                uint64_t nd = (live && have_tile) ? ~b0 : 0ull;
+                                nd &= nvalid >= 64 ? ~0ull : ((1ull << nvalid) - 1ull);
+                                const unsigned lo = __reduce_or_sync(FULL, (unsigned)nd);
+                                const unsigned hi = __reduce_or_sync(FULL, (unsigned)(nd >> 32));
+                                need = ((uint64_t)hi << 32) | lo;
+                            }
                             auto circle_inside = [&](const Split& sp) {
                                 const float rad = sqrtf(sp.u.x * sp.u.x + sp.u.y * sp.u.y + sp.u.z * sp.u.z) + 1e-3f;
                                 return sp.a.x - rad >= lo && sp.a.x + rad < hix && sp.a.y - rad >= lo &&
                                        sp.a.y + rad < hiy && sp.a.z - rad >= lo && sp.a.z + rad < hiz;
                             };
-                            // two moving atoms per pass share each angle's table load (small chunks)
+                            // one moving atom per pass: a single copy of the unrolled lookups keeps the hot
+                            // code small enough for the instruction cache at two CTAs per SM
                             int s = 0;
-                            for (; KC <= 18 && s + 1 < nslot; s += 2) {
-                                const int i0 = q + Q * s, i1 = i0 + Q;
-                                const bool h1 = i1 < nmov;  // i0 < nmov whenever s + 1 < nslot
-                                Split sp[2];
-                                sp[0] = turn(split(ld3(xs, mov[i0], G, ps), gc, kax), pre);
-                                sp[1] = turn(split(ld3(xs, mov[h1 ? i1 : i0], G, ps), gc, kax), pre);
-                                const bool fast = __all_sync(FULL, circle_inside(sp[0]) && (circle_inside(sp[1]) || !h1));
-                                if (h1) {
-                                    score_atoms<KC, MODE, CLIP, 2>(pd, K, bias, sp, fast, cst, acc, pen, box);
-                                } else {
-                                    Split one[1] = {sp[0]};
-                                    score_atoms<KC, MODE, CLIP, 1>(pd, K, bias, one, fast, cst, acc, pen, box);
-                                }
-                            }
                             for (; s < nslot; ++s) {
                                 const int i0 = q + Q * s;
                                 const bool h0 = i0 < nmov;
                                 Split one[1] = {turn(split(ld3(xs, mov[h0 ? i0 : 0], G, ps), gc, kax), pre)};
                                 const bool fast = __all_sync(FULL, circle_inside(one[0]) || !h0);
-                                if (h0) score_atoms<KC, MODE, CLIP, 1>(pd, K, bias, one, fast, cst, acc, pen, box);
+                                if (h0) score_atoms<KC, MODE, CLIP, 1>(pd, K, bias, one, fast, cst, acc, pen, box, need);
                             }
                             // this chunk's bump bits
                             uint64_t bad;
