@@ -293,8 +293,11 @@ constexpr int BW = 7;
 // bytes): the rest of the SM's shared memory serves as L1 cache for the field
 // lookups.
 constexpr int IDX_FLOATS = 68;
+// Entries of the phase's angle table past 64 bw: a chunk's worth for the
+// lookups, and the 12-candidate blocks of the bump tests.
+__host__ __device__ constexpr int ptab_pad(int kc) { return kc > 12 ? kc : 12; }
 __host__ __device__ constexpr int warp_extra_floats(int kc, int bw) {
-    return bw * 64 + 2 * (64 * bw + kc) + IDX_FLOATS;
+    return bw * 64 + 2 * (64 * bw + ptab_pad(kc)) + IDX_FLOATS;
 }
 
 // 32-bit sums over the Q lanes of a pose.
@@ -449,7 +452,7 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
     float* xs = smem + (size_t)warp * (P.slice + warp_extra_floats(KC, P.bw));
     unsigned long long* bump = reinterpret_cast<unsigned long long*>(xs + P.slice);  // [bw][32]
     float2* ptab = reinterpret_cast<float2*>(xs + P.slice + P.bw * 64);             // the phase's (cos, sin)
-    uint8_t* sidx = reinterpret_cast<uint8_t*>(ptab + 64 * P.bw + KC);              // the sweep's index lists
+    uint8_t* sidx = reinterpret_cast<uint8_t*>(ptab + 64 * P.bw + ptab_pad(KC));    // the sweep's index lists
     unsigned long long* col = bump + lane;
     const float shift = MODE == 1 ? 0.0f : 0.5f;
 
@@ -613,7 +616,8 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                         for (int w = 0; w < nw; ++w) col[w * 32] = 0ull;
                         // the phase's angles, the same for every lane; (1, 0) past the end
                         __syncwarp();
-                        for (int j = lane; j < 64 * P.bw + KC; j += 32) ptab[j] = j < ncand ? tab[j] : make_float2(1.f, 0.f);
+                        for (int j = lane; j < 64 * P.bw + ptab_pad(KC); j += 32)
+                            ptab[j] = j < ncand ? tab[j] : make_float2(1.f, 0.f);
                         __syncwarp();
                         {
                             const float lim = thr2 + 0.05f;  // margin over the FP32 error of the bound
@@ -667,21 +671,20 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                                                         (sp.u.x * sp.u.x + sp.u.y * sp.u.y + sp.u.z * sp.u.z);
                                         const float B = 2.f * (dx * sp.u.x + dy * sp.u.y + dz * sp.u.z);
                                         const float C = 2.f * (dx * sp.w.x + dy * sp.w.y + dz * sp.w.z);
-                                        for (int w = 0; w < nw; ++w) {
-                                            const float4* tw = reinterpret_cast<const float4*>(ptab + 64 * w);
-                                            const int gend = min(64, ncand - 64 * w);
-                                            unsigned long long m = 0;
-                                            for (int g = 0; g < gend; g += 16) {
-                                                unsigned m16 = 0;
+                                        // candidates 12 at a time; a block may straddle two 64-bit words
+                                        const float4* tw = reinterpret_cast<const float4*>(ptab);
+                                        for (int g = 0; g < ncand; g += 12) {
+                                            unsigned m12 = 0;
 #pragma unroll
-                                                for (int k = 0; k < 8; ++k) {
-                                                    const float4 t = tw[(g >> 1) + k];
-                                                    if (fmaf(C, t.y, fmaf(B, t.x, A)) < thr2) m16 |= 1u << (2 * k);
-                                                    if (fmaf(C, t.w, fmaf(B, t.z, A)) < thr2) m16 |= 2u << (2 * k);
-                                                }
-                                                m |= (unsigned long long)m16 << g;
+                                            for (int k = 0; k < 6; ++k) {
+                                                const float4 t = tw[(g >> 1) + k];
+                                                if (fmaf(C, t.y, fmaf(B, t.x, A)) < thr2) m12 |= 1u << (2 * k);
+                                                if (fmaf(C, t.w, fmaf(B, t.z, A)) < thr2) m12 |= 2u << (2 * k);
                                             }
-                                            col[w * 32] |= m;
+                                            const int w = g >> 6, sh = g & 63;
+                                            col[w * 32] |= (unsigned long long)m12 << sh;
+                                            if (sh > 52 && w + 1 < P.bw && (m12 >> (64 - sh)))
+                                                col[(w + 1) * 32] |= (unsigned long long)(m12 >> (64 - sh));
                                         }
                                     }
                                 }
