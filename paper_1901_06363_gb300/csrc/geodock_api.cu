@@ -16,6 +16,7 @@
 #include <numeric>
 #include <string>
 #include <tuple>
+#include <thread>
 #include <vector>
 
 #include "../../include/geodock.h"
@@ -65,10 +66,17 @@ struct BatchH {
     std::vector<int> side_m, side_nmov, side_nfixB;  // per side
     std::vector<int> side_off;
     std::vector<int> atom_off;
-    std::unique_ptr<DevBuf> lig, side, idx, xyz0;
+    // every device array of the batch lives in one allocation
+    std::unique_ptr<DevBuf> mem;
+    LigDev* d_lig = nullptr;
+    SideDev* d_side = nullptr;
+    uint8_t* d_idx = nullptr;
+    float* d_xyz0 = nullptr;
     // local refinement: torsions (side away from atom 0, deepest bond first) and bump-pair rows
     int tmax = 0;
-    std::unique_ptr<DevBuf> rlig, rtor, check;
+    RefLigDev* d_rlig = nullptr;
+    RefTorDev* d_rtor = nullptr;
+    uint32_t* d_check = nullptr;
 };
 
 // Everything a batched run needs that depends on (batch, pockets, knobs, tile).
@@ -99,6 +107,8 @@ struct dock_ctx {
     std::map<std::string, dock_tile> tuned;  // autotuned shapes per (batch, knobs)
     DevBuf counter, pose_key, pose_xyz, res, xyz_res;
     DevBuf ref_xyz_in, ref_xyz_out, ref_res;                 // host-memory form of dock_refine
+    void* stage = nullptr;                                   // pinned staging of ligand uploads
+    size_t stage_bytes = 0;
     std::map<std::string, std::unique_ptr<DevBuf>> pocket_sets;  // device pocket arrays per pocket list
     std::map<std::string, std::unique_ptr<Plan>> plans;
     dock_stats stats{};
@@ -108,6 +118,7 @@ struct dock_ctx {
         plans.clear();
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
+        if (stage) cudaFreeHost(stage);
     }
 };
 
@@ -288,6 +299,184 @@ double task_cost(const BatchH& B, int b, const dock_knobs* k, int Q, int kc) {
     return c * std::max(k->repetitions, 1) + B.l[b] * 20.0 / Q;
 }
 
+// Host preparation of ligands [i0, i1) of a batch: topology checks, the two
+// fragments of every rotatable bond (Alg. 1: the left one holds the bond's
+// lower atom index) as per-sweep atom lists, the refinement torsions and the
+// bump-pair rows. Offsets in the outputs are relative to this range.
+struct PrepOut {
+    std::vector<SideDev> sides;
+    std::vector<uint8_t> idx;
+    std::vector<RefTorDev> rtor;
+    std::vector<uint32_t> check;
+    std::vector<int> side_m, side_nmov, side_nfixB;
+    int err = 0;
+    std::string msg;
+};
+
+void prep_range(const dock_ligand_batch* b, int i0, int i1, std::vector<LigDev>& lig, std::vector<RefLigDev>& rlig,
+                PrepOut& out) {
+    char buf[256];
+    auto bad = [&](int code, const char* m) {
+        out.err = code;
+        out.msg = m;
+    };
+    // scratch reused across the range's ligands
+    std::vector<int> deg, off, nbr, depth, queue, stack;
+    std::vector<char> left;
+    std::vector<uint32_t> lw, rw;
+    std::vector<std::tuple<int, int, int>> tor_depth;  // (depth of c, torsion, moving side)
+    for (int i = i0; i < i1; ++i) {
+        const int a0 = b->atom_off[i], l = b->atom_off[i + 1] - a0;
+        const int e0 = b->bond_off[i], ne = b->bond_off[i + 1] - e0;
+        const int r0 = b->rot_off[i], nr = b->rot_off[i + 1] - r0;
+        if (l < 1 || l > DOCK_MAX_ATOMS) {
+            snprintf(buf, sizeof buf, "ligand %d: %d atoms", i, l);
+            return bad(DOCK_ERR_INVALID_ARG, buf);
+        }
+        if (ne < 0 || nr < 0 || (ne > 0 && !b->bonds) || (nr > 0 && !b->rot)) {
+            snprintf(buf, sizeof buf, "ligand %d: bad bond/rotamer offsets", i);
+            return bad(DOCK_ERR_INVALID_ARG, buf);
+        }
+        // adjacency in CSR form
+        deg.assign(l + 1, 0);
+        for (int e = 0; e < ne; ++e) {
+            const int u = b->bonds[2 * (e0 + e)], v = b->bonds[2 * (e0 + e) + 1];
+            if (u < 0 || v < 0 || u >= l || v >= l || u == v) {
+                snprintf(buf, sizeof buf, "ligand %d: bond %d has bad atoms", i, e);
+                return bad(DOCK_ERR_INVALID_ARG, buf);
+            }
+            ++deg[u];
+            ++deg[v];
+        }
+        off.assign(l + 1, 0);
+        for (int a = 0; a < l; ++a) off[a + 1] = off[a] + deg[a];
+        nbr.resize(2 * ne);
+        for (int a = 0; a < l; ++a) deg[a] = off[a];
+        for (int e = 0; e < ne; ++e) {
+            const int u = b->bonds[2 * (e0 + e)], v = b->bonds[2 * (e0 + e) + 1];
+            nbr[deg[u]++] = v;
+            nbr[deg[v]++] = u;
+        }
+        double g[3] = {0, 0, 0};
+        for (int a = 0; a < l; ++a)
+            for (int d = 0; d < 3; ++d) {
+                const float x = b->xyz[3 * (a0 + a) + d];
+                if (!std::isfinite(x) || std::fabs(x) > 1e5f) {
+                    snprintf(buf, sizeof buf, "ligand %d: coordinate out of range", i);
+                    return bad(DOCK_ERR_INVALID_ARG, buf);
+                }
+                g[d] += (double)x;
+            }
+        LigDev& L = lig[i];
+        L.atom_off = a0;
+        L.l = l;
+        L.nside = 2 * nr;
+        L.side_off = (int)out.sides.size();
+        for (int d = 0; d < 3; ++d) L.g[d] = g[d] / l;
+        L.id = b->ids ? b->ids[i] : b->id_base + i;
+        // graph depth from atom 0 (refinement order)
+        depth.assign(l, -1);
+        queue.assign(1, 0);
+        depth[0] = 0;
+        for (size_t h = 0; h < queue.size(); ++h)
+            for (int k = off[queue[h]]; k < off[queue[h] + 1]; ++k)
+                if (depth[nbr[k]] < 0) {
+                    depth[nbr[k]] = depth[queue[h]] + 1;
+                    queue.push_back(nbr[k]);
+                }
+        const int wpr = (l + 31) / 32;
+        RefLigDev& RL = rlig[i];
+        RL.tor_off = (int)out.rtor.size();
+        RL.T = nr;
+        RL.check_off = (int)out.check.size();
+        RL.wpr = wpr;
+        out.check.resize(out.check.size() + (size_t)l * wpr, 0u);
+        tor_depth.clear();
+        for (int r = 0; r < nr; ++r) {
+            const int e = b->rot[r0 + r];
+            if (e < 0 || e >= ne) {
+                snprintf(buf, sizeof buf, "ligand %d: rotatable bond index %d", i, e);
+                return bad(DOCK_ERR_INVALID_ARG, buf);
+            }
+            int u = b->bonds[2 * (e0 + e)], v = b->bonds[2 * (e0 + e) + 1];
+            if (u > v) std::swap(u, v);
+            // left fragment: atoms reachable from u without crossing (u, v)
+            left.assign(l, 0);
+            stack.assign(1, u);
+            left[u] = 1;
+            while (!stack.empty()) {
+                const int x = stack.back();
+                stack.pop_back();
+                for (int k = off[x]; k < off[x + 1]; ++k) {
+                    const int y = nbr[k];
+                    if ((x == u && y == v) || (x == v && y == u)) continue;
+                    if (!left[y]) {
+                        left[y] = 1;
+                        stack.push_back(y);
+                    }
+                }
+            }
+            if (left[v]) {
+                snprintf(buf, sizeof buf, "ligand %d: rotatable bond %d lies on a ring", i, e);
+                return bad(DOCK_ERR_TOPOLOGY, buf);
+            }
+            // refinement torsion: the side without atom 0 moves (side 1 = right fragment when atom 0 is left)
+            tor_depth.emplace_back(depth[left[0] ? v : u], r, left[0] ? 1 : 0);
+            // bump-pair rows: every pair this torsion moves
+            lw.assign(wpr, 0u);
+            rw.assign(wpr, 0u);
+            for (int a = 0; a < l; ++a) {
+                if (left[a] && a != u) lw[a >> 5] |= 1u << (a & 31);
+                if (!left[a] && a != v) rw[a >> 5] |= 1u << (a & 31);
+            }
+            uint32_t* rows = out.check.data() + RL.check_off;
+            for (int a = 0; a < l; ++a) {
+                const std::vector<uint32_t>* other = (lw[a >> 5] >> (a & 31)) & 1u   ? &rw
+                                                     : (rw[a >> 5] >> (a & 31)) & 1u ? &lw
+                                                                                      : nullptr;
+                if (other)
+                    for (int w = 0; w < wpr; ++w) rows[(size_t)a * wpr + w] |= (*other)[w];
+            }
+            for (int side = 0; side < 2; ++side) {
+                // side 0: the left fragment moves (c = u, b = v); side 1: the right one (c = v, b = u)
+                const int c = side == 0 ? u : v, bb = side == 0 ? v : u;
+                SideDev sd{};
+                sd.c = (uint8_t)c;
+                sd.b = (uint8_t)bb;
+                sd.mov_off = (int)out.idx.size();
+                int m = 0;
+                for (int a = 0; a < l; ++a) {
+                    const bool moving = side == 0 ? left[a] != 0 : left[a] == 0;
+                    if (!moving) continue;
+                    ++m;
+                    if (a != c) out.idx.push_back((uint8_t)a);
+                }
+                sd.m = (uint8_t)m;
+                sd.nmov = (uint8_t)(m - 1);
+                sd.fix_off = (int)out.idx.size();
+                for (int a = 0; a < l; ++a) {
+                    const bool moving = side == 0 ? left[a] != 0 : left[a] == 0;
+                    if (!moving && a != bb) out.idx.push_back((uint8_t)a);
+                }
+                out.idx.push_back((uint8_t)bb);
+                out.idx.push_back((uint8_t)c);
+                sd.nfixB = (uint8_t)(l - m - 1);
+                sd.nfixS = (uint8_t)(l - m + 1);
+                out.sides.push_back(sd);
+                out.side_m.push_back(m);
+                out.side_nmov.push_back(m - 1);
+                out.side_nfixB.push_back(l - m - 1);
+            }
+        }
+        // deepest bond first, ties in bond order
+        std::stable_sort(tor_depth.begin(), tor_depth.end(),
+                         [](const std::tuple<int, int, int>& x, const std::tuple<int, int, int>& y) {
+                             return std::get<0>(x) > std::get<0>(y);
+                         });
+        for (const auto& td : tor_depth) out.rtor.push_back({2 * std::get<1>(td) + std::get<2>(td), std::get<1>(td)});
+    }
+}
+
 }  // namespace
 
 // ======================================================================== API
@@ -415,172 +604,110 @@ int dock_upload_ligands(dock_ctx* ctx, const dock_ligand_batch* b, int* batch_id
     if (b->n < 0) return fail(ctx, DOCK_ERR_INVALID_ARG, "batch: n < 0");
     if (b->n > 0 && (!b->atom_off || !b->xyz || !b->bond_off || !b->rot_off))
         return fail(ctx, DOCK_ERR_INVALID_ARG, "batch: NULL array");
-    CK(cudaSetDevice(ctx->device));
-    BatchH B;
-    B.n = b->n;
-    std::vector<LigDev> lig(b->n);
-    std::vector<SideDev> sides;
-    std::vector<uint8_t> idx;
-    std::vector<RefLigDev> rlig(b->n);
-    std::vector<RefTorDev> rtor;
-    std::vector<uint32_t> check;
     if (b->n > 0 && (b->atom_off[0] != 0 || b->bond_off[0] != 0 || b->rot_off[0] != 0))
         return fail(ctx, DOCK_ERR_INVALID_ARG, "batch: offsets must start at 0");
-    for (int i = 0; i < b->n; ++i) {
-        int a0 = b->atom_off[i], l = b->atom_off[i + 1] - a0;
-        int e0 = b->bond_off[i], ne = b->bond_off[i + 1] - e0;
-        int r0 = b->rot_off[i], nr = b->rot_off[i + 1] - r0;
-        if (l < 1 || l > DOCK_MAX_ATOMS) return fail(ctx, DOCK_ERR_INVALID_ARG, "ligand %d: %d atoms", i, l);
-        if (ne < 0 || nr < 0 || (ne > 0 && !b->bonds) || (nr > 0 && !b->rot))
-            return fail(ctx, DOCK_ERR_INVALID_ARG, "ligand %d: bad bond/rotamer offsets", i);
-        std::vector<std::vector<int>> adj(l);
-        for (int e = 0; e < ne; ++e) {
-            int u = b->bonds[2 * (e0 + e)], v = b->bonds[2 * (e0 + e) + 1];
-            if (u < 0 || v < 0 || u >= l || v >= l || u == v)
-                return fail(ctx, DOCK_ERR_INVALID_ARG, "ligand %d: bond %d has bad atoms", i, e);
-            adj[u].push_back(v);
-            adj[v].push_back(u);
-        }
-        double g[3] = {0, 0, 0};
-        for (int a = 0; a < l; ++a)
-            for (int d = 0; d < 3; ++d) {
-                float x = b->xyz[3 * (a0 + a) + d];
-                if (!std::isfinite(x) || std::fabs(x) > 1e5f)
-                    return fail(ctx, DOCK_ERR_INVALID_ARG, "ligand %d: coordinate out of range", i);
-                g[d] += (double)x;
-            }
-        LigDev& L = lig[i];
-        L.atom_off = a0;
-        L.l = l;
-        L.nside = 2 * nr;
-        L.side_off = (int)sides.size();
-        for (int d = 0; d < 3; ++d) L.g[d] = g[d] / l;
-        L.id = b->ids ? b->ids[i] : b->id_base + i;
-        B.l.push_back(l);
-        B.nside.push_back(2 * nr);
-        B.side_off.push_back((int)sides.size());
-        B.atom_off.push_back(a0);
-        B.lmax = std::max(B.lmax, l);
-        B.tmax = std::max(B.tmax, nr);
-        // graph depth from atom 0 (refinement order) and the bump-pair rows
-        std::vector<int> depth(l, -1);
-        {
-            std::vector<int> q{0};
-            depth[0] = 0;
-            for (size_t h = 0; h < q.size(); ++h)
-                for (int y : adj[q[h]])
-                    if (depth[y] < 0) {
-                        depth[y] = depth[q[h]] + 1;
-                        q.push_back(y);
-                    }
-        }
-        const int wpr = (l + 31) / 32;
-        RefLigDev& RL = rlig[i];
-        RL.tor_off = (int)rtor.size();
-        RL.T = nr;
-        RL.check_off = (int)check.size();
-        RL.wpr = wpr;
-        check.resize(check.size() + (size_t)l * wpr, 0u);
-        std::vector<std::tuple<int, int, int>> tor_depth;  // (depth of c, torsion, moving side)
-        for (int r = 0; r < nr; ++r) {
-            int e = b->rot[r0 + r];
-            if (e < 0 || e >= ne) return fail(ctx, DOCK_ERR_INVALID_ARG, "ligand %d: rotatable bond index %d", i, e);
-            int u = b->bonds[2 * (e0 + e)], v = b->bonds[2 * (e0 + e) + 1];
-            if (u > v) std::swap(u, v);
-            // left fragment: atoms reachable from u without crossing (u, v)
-            std::vector<char> left(l, 0);
-            std::vector<int> st{u};
-            left[u] = 1;
-            while (!st.empty()) {
-                int x = st.back();
-                st.pop_back();
-                for (int y : adj[x]) {
-                    if ((x == u && y == v) || (x == v && y == u)) continue;
-                    if (!left[y]) {
-                        left[y] = 1;
-                        st.push_back(y);
-                    }
-                }
-            }
-            if (left[v]) return fail(ctx, DOCK_ERR_TOPOLOGY, "ligand %d: rotatable bond %d lies on a ring", i, e);
-            // refinement torsion: the side without atom 0 moves (side 1 = right fragment when atom 0 is left)
-            tor_depth.emplace_back(depth[left[0] ? v : u], r, left[0] ? 1 : 0);
-            {
-                std::vector<uint32_t> lw(wpr, 0u), rw(wpr, 0u);
-                for (int a = 0; a < l; ++a) {
-                    if (left[a] && a != u) lw[a >> 5] |= 1u << (a & 31);
-                    if (!left[a] && a != v) rw[a >> 5] |= 1u << (a & 31);
-                }
-                uint32_t* rows = check.data() + RL.check_off;
-                for (int a = 0; a < l; ++a) {
-                    const std::vector<uint32_t>* other = (lw[a >> 5] >> (a & 31)) & 1u   ? &rw
-                                                         : (rw[a >> 5] >> (a & 31)) & 1u ? &lw
-                                                                                          : nullptr;
-                    if (other)
-                        for (int w = 0; w < wpr; ++w) rows[(size_t)a * wpr + w] |= (*other)[w];
-                }
-            }
-            for (int side = 0; side < 2; ++side) {
-                // side 0: the left fragment moves (c = u, b = v); side 1: the right one (c = v, b = u)
-                int c = side == 0 ? u : v, bb = side == 0 ? v : u;
-                SideDev sd{};
-                sd.c = (uint8_t)c;
-                sd.b = (uint8_t)bb;
-                sd.mov_off = (int)idx.size();
-                int m = 0;
-                for (int a = 0; a < l; ++a) {
-                    bool moving = side == 0 ? left[a] != 0 : left[a] == 0;
-                    if (!moving) continue;
-                    ++m;
-                    if (a != c) idx.push_back((uint8_t)a);
-                }
-                sd.m = (uint8_t)m;
-                sd.nmov = (uint8_t)(m - 1);
-                sd.fix_off = (int)idx.size();
-                for (int a = 0; a < l; ++a) {
-                    bool moving = side == 0 ? left[a] != 0 : left[a] == 0;
-                    if (!moving && a != bb) idx.push_back((uint8_t)a);
-                }
-                idx.push_back((uint8_t)bb);
-                idx.push_back((uint8_t)c);
-                sd.nfixB = (uint8_t)(l - m - 1);
-                sd.nfixS = (uint8_t)(l - m + 1);
-                sides.push_back(sd);
-                B.side_m.push_back(m);
-                B.side_nmov.push_back(m - 1);
-                B.side_nfixB.push_back(l - m - 1);
-            }
-        }
-        // deepest bond first, ties in bond order
-        std::stable_sort(tor_depth.begin(), tor_depth.end(),
-                         [](const std::tuple<int, int, int>& a, const std::tuple<int, int, int>& c) {
-                             return std::get<0>(a) > std::get<0>(c);
-                         });
-        for (const auto& td : tor_depth) rtor.push_back({2 * std::get<1>(td) + std::get<2>(td), std::get<1>(td)});
+    CK(cudaSetDevice(ctx->device));
+    const int n = b->n;
+    BatchH B;
+    B.n = n;
+    std::vector<LigDev> lig(n);
+    std::vector<RefLigDev> rlig(n);
+    // the ligands are independent: ranges of them are prepared in parallel, then joined in order
+    const int hw = std::max(1, (int)std::thread::hardware_concurrency());
+    const int nt = std::max(1, std::min(hw, n / 64));
+    std::vector<PrepOut> parts(nt);
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t) {
+        const int i0 = (int)((int64_t)n * t / nt), i1 = (int)((int64_t)n * (t + 1) / nt);
+        if (t + 1 < nt)
+            pool.emplace_back([&, t, i0, i1]() { prep_range(b, i0, i1, lig, rlig, parts[t]); });
+        else
+            prep_range(b, i0, i1, lig, rlig, parts[t]);
     }
-    B.natoms = b->n > 0 ? b->atom_off[b->n] : 0;
+    for (auto& th : pool) th.join();
+    for (const PrepOut& o : parts)
+        if (o.err) return fail(ctx, o.err, "%s", o.msg.c_str());
+    size_t nside = 0, nidx = 0, ntor = 0, nchk = 0;
+    for (const PrepOut& o : parts) {
+        nside += o.sides.size();
+        nidx += o.idx.size();
+        ntor += o.rtor.size();
+        nchk += o.check.size();
+    }
+    std::vector<SideDev> sides;
+    std::vector<uint8_t> idx;
+    std::vector<RefTorDev> rtor;
+    std::vector<uint32_t> check;
+    sides.reserve(nside);
+    idx.reserve(nidx);
+    rtor.reserve(ntor);
+    check.reserve(nchk);
+    for (int t = 0; t < nt; ++t) {
+        const PrepOut& o = parts[t];
+        const int i0 = (int)((int64_t)n * t / nt), i1 = (int)((int64_t)n * (t + 1) / nt);
+        const int sb = (int)sides.size(), ib = (int)idx.size(), tb = (int)rtor.size(), cb = (int)check.size();
+        for (int i = i0; i < i1; ++i) {
+            lig[i].side_off += sb;
+            rlig[i].tor_off += tb;
+            rlig[i].check_off += cb;
+        }
+        for (SideDev sd : o.sides) {
+            sd.mov_off += ib;
+            sd.fix_off += ib;
+            sides.push_back(sd);
+        }
+        idx.insert(idx.end(), o.idx.begin(), o.idx.end());
+        rtor.insert(rtor.end(), o.rtor.begin(), o.rtor.end());  // sides index the ligand's own
+        check.insert(check.end(), o.check.begin(), o.check.end());
+        B.side_m.insert(B.side_m.end(), o.side_m.begin(), o.side_m.end());
+        B.side_nmov.insert(B.side_nmov.end(), o.side_nmov.begin(), o.side_nmov.end());
+        B.side_nfixB.insert(B.side_nfixB.end(), o.side_nfixB.begin(), o.side_nfixB.end());
+    }
+    for (int i = 0; i < n; ++i) {
+        B.l.push_back(lig[i].l);
+        B.nside.push_back(lig[i].nside);
+        B.side_off.push_back(lig[i].side_off);
+        B.atom_off.push_back(lig[i].atom_off);
+        B.lmax = std::max(B.lmax, lig[i].l);
+        B.tmax = std::max(B.tmax, rlig[i].T);
+    }
+    B.natoms = n > 0 ? b->atom_off[n] : 0;
     B.nside_total = (int)sides.size();
-    B.lig.reset(new DevBuf());
-    B.side.reset(new DevBuf());
-    B.idx.reset(new DevBuf());
-    B.xyz0.reset(new DevBuf());
-    CK(B.lig->ensure(lig.size() * sizeof(LigDev)));
-    CK(B.side->ensure(sides.size() * sizeof(SideDev)));
-    CK(B.idx->ensure(idx.size()));
-    CK(B.xyz0->ensure((size_t)B.natoms * 3 * sizeof(float)));
-    if (!lig.empty()) CK(cudaMemcpy(B.lig->p, lig.data(), lig.size() * sizeof(LigDev), cudaMemcpyHostToDevice));
-    if (!sides.empty()) CK(cudaMemcpy(B.side->p, sides.data(), sides.size() * sizeof(SideDev), cudaMemcpyHostToDevice));
-    if (!idx.empty()) CK(cudaMemcpy(B.idx->p, idx.data(), idx.size(), cudaMemcpyHostToDevice));
-    if (B.natoms) CK(cudaMemcpy(B.xyz0->p, b->xyz, (size_t)B.natoms * 3 * sizeof(float), cudaMemcpyHostToDevice));
-    B.rlig.reset(new DevBuf());
-    B.rtor.reset(new DevBuf());
-    B.check.reset(new DevBuf());
-    CK(B.rlig->ensure(std::max<size_t>(1, rlig.size()) * sizeof(RefLigDev)));
-    CK(B.rtor->ensure(std::max<size_t>(1, rtor.size()) * sizeof(RefTorDev)));
-    CK(B.check->ensure(std::max<size_t>(1, check.size()) * sizeof(uint32_t)));
-    if (!rlig.empty()) CK(cudaMemcpy(B.rlig->p, rlig.data(), rlig.size() * sizeof(RefLigDev), cudaMemcpyHostToDevice));
-    if (!rtor.empty()) CK(cudaMemcpy(B.rtor->p, rtor.data(), rtor.size() * sizeof(RefTorDev), cudaMemcpyHostToDevice));
-    if (!check.empty()) CK(cudaMemcpy(B.check->p, check.data(), check.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    // one device allocation and one copy from a pinned staging buffer
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t o_lig = 0, o_side = al(o_lig + lig.size() * sizeof(LigDev));
+    const size_t o_idx = al(o_side + sides.size() * sizeof(SideDev));
+    const size_t o_xyz = al(o_idx + idx.size());
+    const size_t o_rlig = al(o_xyz + (size_t)B.natoms * 3 * sizeof(float));
+    const size_t o_rtor = al(o_rlig + rlig.size() * sizeof(RefLigDev));
+    const size_t o_chk = al(o_rtor + rtor.size() * sizeof(RefTorDev));
+    const size_t total = al(o_chk + check.size() * sizeof(uint32_t)) + 256;
+    if (ctx->stage_bytes < total) {
+        if (ctx->stage) cudaFreeHost(ctx->stage);
+        ctx->stage = nullptr;
+        ctx->stage_bytes = 0;
+        CK(cudaHostAlloc(&ctx->stage, total, cudaHostAllocDefault));
+        ctx->stage_bytes = total;
+    }
+    uint8_t* h = static_cast<uint8_t*>(ctx->stage);
+    std::memcpy(h + o_lig, lig.data(), lig.size() * sizeof(LigDev));
+    std::memcpy(h + o_side, sides.data(), sides.size() * sizeof(SideDev));
+    std::memcpy(h + o_idx, idx.data(), idx.size());
+    if (B.natoms) std::memcpy(h + o_xyz, b->xyz, (size_t)B.natoms * 3 * sizeof(float));
+    std::memcpy(h + o_rlig, rlig.data(), rlig.size() * sizeof(RefLigDev));
+    std::memcpy(h + o_rtor, rtor.data(), rtor.size() * sizeof(RefTorDev));
+    std::memcpy(h + o_chk, check.data(), check.size() * sizeof(uint32_t));
+    B.mem.reset(new DevBuf());
+    CK(B.mem->ensure(total));
+    CK(cudaMemcpy(B.mem->p, h, total, cudaMemcpyHostToDevice));
+    uint8_t* d = B.mem->as<uint8_t>();
+    B.d_lig = reinterpret_cast<LigDev*>(d + o_lig);
+    B.d_side = reinterpret_cast<SideDev*>(d + o_side);
+    B.d_idx = d + o_idx;
+    B.d_xyz0 = reinterpret_cast<float*>(d + o_xyz);
+    B.d_rlig = reinterpret_cast<RefLigDev*>(d + o_rlig);
+    B.d_rtor = reinterpret_cast<RefTorDev*>(d + o_rtor);
+    B.d_check = reinterpret_cast<uint32_t*>(d + o_chk);
     B.live = true;
     ctx->batches.push_back(std::move(B));
     *batch_id = (int)ctx->batches.size() - 1;
@@ -741,10 +868,10 @@ int get_plan(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const doc
         }
     }
     SweepParams& P = pl->P;
-    P.lig = B.lig->as<LigDev>();
-    P.side = B.side->as<SideDev>();
-    P.idx = B.idx->as<uint8_t>();
-    P.xyz0 = B.xyz0->as<float>();
+    P.lig = B.d_lig;
+    P.side = B.d_side;
+    P.idx = B.d_idx;
+    P.xyz0 = B.d_xyz0;
     P.pockets = pl->pockets->as<PocketDev>();
     P.tasks = pl->tasks->as<int2>();
     P.ntask = pl->ntask;
@@ -1156,10 +1283,10 @@ extern "C" int dock_run_static(dock_ctx* ctx, int batch_id, int pocket_id, const
     }
 
     SweepParams P{};
-    P.lig = B.lig->as<LigDev>();
-    P.side = B.side->as<SideDev>();
-    P.idx = B.idx->as<uint8_t>();
-    P.xyz0 = B.xyz0->as<float>();
+    P.lig = B.d_lig;
+    P.side = B.d_side;
+    P.idx = B.d_idx;
+    P.xyz0 = B.d_xyz0;
     P.pockets = reinterpret_cast<const PocketDev*>(base + kOffPocket);
     P.tasks = reinterpret_cast<const int2*>(base + kOffTasks);
     P.ntask = ntask;
@@ -1232,11 +1359,11 @@ int check_pocket(dock_ctx* ctx, int pocket_id) {
 ScoreParams score_params(dock_ctx* ctx, const BatchH& B, const PocketDev* pocket_dev) {
     (void)ctx;
     ScoreParams P{};
-    P.lig = B.lig->as<LigDev>();
-    P.side = B.side->as<SideDev>();
-    P.idx = B.idx->as<uint8_t>();
-    P.rlig = B.rlig->as<RefLigDev>();
-    P.rtor = B.rtor->as<RefTorDev>();
+    P.lig = B.d_lig;
+    P.side = B.d_side;
+    P.idx = B.d_idx;
+    P.rlig = B.d_rlig;
+    P.rtor = B.d_rtor;
     P.pocket = pocket_dev;
     P.nlig = B.n;
     return P;
@@ -1290,12 +1417,12 @@ int refine_impl(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const 
         res = ctx->ref_res.as<float>();
     }
     RefineParams P{};
-    P.lig = B.lig->as<LigDev>();
-    P.side = B.side->as<SideDev>();
-    P.idx = B.idx->as<uint8_t>();
-    P.rlig = B.rlig->as<RefLigDev>();
-    P.rtor = B.rtor->as<RefTorDev>();
-    P.check = B.check->as<uint32_t>();
+    P.lig = B.d_lig;
+    P.side = B.d_side;
+    P.idx = B.d_idx;
+    P.rlig = B.d_rlig;
+    P.rtor = B.d_rtor;
+    P.check = B.d_check;
     P.pockets = pset;
     P.npairs = npairs;
     P.nlig = B.n;
