@@ -5,8 +5,8 @@ per configuration and validated leave-one-pocket-out.
     python -m paper_1901_06363_gb300.knobsweep [--ligands 100000] [--fit-ligands 2000] [--out FILE]
 
 Inputs are the seeded synthetic workloads: lognormal ligands (median 32 atoms, Poisson(6) rotatable
-bonds) on the 64^3 ellipsoid pocket for the sweep, and four pockets of 48^3-128^3 x four ligand groups
-(quartiles of atoms x rotatable bonds) for the model. Every run is a batched dock_run timed with CUDA
+bonds) on the 64^3 ellipsoid pocket for the sweep, and that pocket plus four pockets of 48^3-128^3 x four
+ligand groups (quartiles of atoms x rotatable bonds) for the model. Every run is a batched dock_run timed with CUDA
 events on its stream after one warm-up run of the same plan; the plain per-pair form is timed on a
 subset. Prints one JSON document.
 """
@@ -36,7 +36,7 @@ def _timed_run(dk, bid, pids, kn, n, natoms, out, xyz, stream, torch):
     return e0.elapsed_time(e1) / 1e3
 
 
-def run(ligands=100_000, fit_ligands=2_000, plain_ligands=128, seed=3, combos=None, log=None):
+def run(ligands=100_000, fit_ligands=4_000, plain_ligands=128, seed=3, combos=None, log=None):
     import torch
 
     import synth
@@ -80,7 +80,7 @@ def run(ligands=100_000, fit_ligands=2_000, plain_ligands=128, seed=3, combos=No
 
     # ---- Eq. 4: per configuration, times over pockets x ligand groups
     pks = C.multi_pocket_pockets()
-    fit_pockets = [pks[i] for i in (0, 4, 8, 12)]  # 48^3, 64^3, 96^3, 128^3
+    fit_pockets = [pk] + [pks[i] for i in (0, 4, 8, 12)]  # the sweep's pocket, then 48^3, 64^3, 96^3, 128^3
     fpids = [dk.init_pocket(p) for p in fit_pockets]
     fb = C.sweep_batch(4 * fit_ligands, seed + 100, id0=10_000_000)
     l, t = fb.sizes()
@@ -149,7 +149,7 @@ def run(ligands=100_000, fit_ligands=2_000, plain_ligands=128, seed=3, combos=No
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--ligands", type=int, default=100_000)
-    ap.add_argument("--fit-ligands", type=int, default=2_000)
+    ap.add_argument("--fit-ligands", type=int, default=4_000)
     ap.add_argument("--plain-ligands", type=int, default=128)
     ap.add_argument("--out", default=None)
     args = ap.parse_args()

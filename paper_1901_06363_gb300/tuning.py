@@ -19,7 +19,8 @@ score of the top 1 % of the ligands.
 Knob selection (the paper delegates it to its autotuner): among the
 configurations whose predicted time fits the budget, take the one with the
 lowest degradation; when none fits, take the fastest, which then docks the
-fraction budget / t of the database.
+fraction budget / t of the database. A configuration whose model predicts a
+non-positive time (outside its training range) is left out.
 
 Host-side arithmetic only: the times come from runs of the CUDA path.
 """
@@ -126,7 +127,9 @@ class Choice:
 def select(models, degr, x, nu, budget_s) -> Choice:
     """The configuration of lowest degradation whose predicted time for nu ligands fits the budget;
     if none fits, the fastest one and the fraction of the database it docks in the budget."""
+    # a model that predicts no time at all has left its training range: it gives no estimate
     t = {k: m.predict(x, nu) for k, m in models.items() if k in degr}
+    t = {k: tk for k, tk in t.items() if tk > 0}
     fits = [k for k, tk in t.items() if tk <= budget_s]
     if fits:
         k = min(fits, key=lambda c: (degr[c], t[c]))

@@ -77,3 +77,15 @@ def test_select_under_budget():
     assert c.config == "C"
     c = tuning.select(models, degr, None, 10, 5.0)
     assert c.config == "A" and c.completion == pytest.approx(0.5)
+
+
+def test_select_ignores_models_outside_their_range():
+    class M:
+        def __init__(self, t):
+            self.t = t
+
+        def predict(self, x, nu):
+            return self.t * nu
+
+    c = tuning.select({"A": M(-1.0), "B": M(2.0)}, {"A": 0.0, "B": 5.0}, None, 10, 100.0)
+    assert c.config == "B"
