@@ -926,10 +926,14 @@ int get_plan(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const doc
 // Enqueue one batched run: reset the queue, persistent sweep, finalize.
 int enqueue_batched(dock_ctx* ctx, Plan* pl, const dock_knobs* k, cudaStream_t s) {
     CK(cudaMemsetAsync(ctx->counter.p, 0, sizeof(unsigned), s));
-    // external event records become event nodes when this is captured into a graph
-    CK(cudaEventRecordWithFlags(ctx->ev0, s, cudaEventRecordExternal));
+    // external event records become event nodes when this is captured into a graph; outside a
+    // capture (the autotuner) they are plain records
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &cs));
+    const unsigned flags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+    CK(cudaEventRecordWithFlags(ctx->ev0, s, flags));
     if (pl->ntask > 0) CK(launch_sweep(pl->kc, pl->P, k->score_mode, k->clip_box, pl->grid, pl->block, pl->smem, s));
-    CK(cudaEventRecordWithFlags(ctx->ev1, s, cudaEventRecordExternal));
+    CK(cudaEventRecordWithFlags(ctx->ev1, s, flags));
     if (pl->npairs > 0) {
         finalize_kernel<<<(pl->npairs + 3) / 4, 128, 0, s>>>(pl->F);
         CK(cudaGetLastError());
@@ -1136,7 +1140,12 @@ int dock_autotune(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs* 
                     ok = enqueue_batched(ctx, pl, k, s) == DOCK_OK;
                     cudaEventRecord(e1, s);
                     ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
-                    cudaEventElapsedTime(&ms, e0, e1);
+                    ok = ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+                }
+                if (!ok) {
+                    // a shape this device cannot run: drop its error and its plan, keep going
+                    cudaStreamSynchronize(s);
+                    cudaGetLastError();
                 }
                 if (ok && ms < best_ms) {
                     best_ms = ms;

@@ -2,13 +2,15 @@
 degradation (Eq. 5) over the (step, initial poses, repetitions) grid, and the Eq. 4 time model fitted
 per configuration and validated leave-one-pocket-out.
 
-    python -m paper_1901_06363_gb300.knobsweep [--ligands 100000] [--fit-ligands 2000] [--out FILE]
+    python -m paper_1901_06363_gb300.knobsweep [--ligands 100000] [--fit-ligands 4000] [--out FILE]
+                                               [--checkpoint DIR]
 
 Inputs are the seeded synthetic workloads: lognormal ligands (median 32 atoms, Poisson(6) rotatable
 bonds) on the 64^3 ellipsoid pocket for the sweep, and that pocket plus four pockets of 48^3-128^3 x four
 ligand groups (quartiles of atoms x rotatable bonds) for the model. Every run is a batched dock_run timed with CUDA
 events on its stream after one warm-up run of the same plan; the plain per-pair form is timed on a
-subset. Prints one JSON document.
+subset. Prints one JSON document. With --checkpoint, every finished shard (one configuration on the
+sweep set, its plain-form timing, one fit row) is kept in DIR and skipped when the run is restarted.
 """
 from __future__ import annotations
 
@@ -25,6 +27,29 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+class Checkpoint:
+    """Finished result shards under a directory (one .npz per key); a restarted run loads them
+    instead of recomputing. Without a directory every shard is computed."""
+
+    def __init__(self, path=None):
+        self.path = path
+        if path:
+            os.makedirs(path, exist_ok=True)
+
+    def get(self, key, compute):
+        if not self.path:
+            return compute()
+        f = os.path.join(self.path, key + ".npz")
+        if os.path.exists(f):
+            with np.load(f) as z:
+                return {k: z[k] for k in z.files}
+        res = compute()
+        tmp = os.path.join(self.path, key + ".part.npz")
+        np.savez(tmp, **res)
+        os.replace(tmp, f)  # a shard appears whole or not at all
+        return res
+
+
 def _timed_run(dk, bid, pids, kn, n, natoms, out, xyz, stream, torch):
     dk.run(bid, pids, kn, n, natoms, out=out, xyz_out=xyz, stream=stream)  # warm: builds and captures the plan
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -36,7 +61,7 @@ def _timed_run(dk, bid, pids, kn, n, natoms, out, xyz, stream, torch):
     return e0.elapsed_time(e1) / 1e3
 
 
-def run(ligands=100_000, fit_ligands=4_000, plain_ligands=128, seed=3, combos=None, log=None):
+def run(ligands=100_000, fit_ligands=4_000, plain_ligands=128, seed=3, combos=None, log=None, checkpoint=None):
     import torch
 
     import synth
@@ -47,6 +72,8 @@ def run(ligands=100_000, fit_ligands=4_000, plain_ligands=128, seed=3, combos=No
     stream = torch.cuda.current_stream()
     dk = Docker(torch.cuda.current_device())
     say = log or (lambda *a: None)
+    ck = Checkpoint(checkpoint)
+    tag = lambda k: f"{k[0]:g}_{k[1]}_{k[2]}"  # noqa: E731
 
     # ---- sweep: every combination on the full ligand set, one pocket
     pk = synth.pocket(1 + 7, 64, 0.5, C.ELLIPSOID)
@@ -61,9 +88,13 @@ def run(ligands=100_000, fit_ligands=4_000, plain_ligands=128, seed=3, combos=No
     key = lambda k: (k["hp_step"], k["n_poses"], k["repetitions"])  # noqa: E731
     sweep = {}
     for kn in combos:
-        t = _timed_run(dk, bid, [pid], kn, n, natoms, out, xyz, stream, torch)
-        sc = out.view(torch.float32).reshape(-1, 4)[:, 0].cpu().numpy().copy()
-        sweep[key(kn)] = dict(seconds=t, ligands_per_s=n / t, scores=sc)
+        def one(kn=kn):
+            t = _timed_run(dk, bid, [pid], kn, n, natoms, out, xyz, stream, torch)
+            sc = out.view(torch.float32).reshape(-1, 4)[:, 0].cpu().numpy().copy()
+            return dict(seconds=np.float64(t), scores=sc)
+        r = ck.get(f"sweep_{n}_{tag(key(kn))}", one)
+        t = float(r["seconds"])
+        sweep[key(kn)] = dict(seconds=t, ligands_per_s=n / t, scores=r["scores"])
         say(f"sweep {key(kn)}: {t:.3f} s, {n / t:.0f} ligands/s")
     base = max(sweep, key=lambda c: (-c[0], c[1], c[2]))  # finest step, most poses, most repetitions
     # plain per-pair form on a subset, per configuration
@@ -73,8 +104,9 @@ def run(ligands=100_000, fit_ligands=4_000, plain_ligands=128, seed=3, combos=No
     so = torch.empty(plain_ligands * 4, dtype=torch.int32, device=dev)
     sx = torch.empty(sat * 3, dtype=torch.float32, device=dev)
     for kn in combos:
-        t = _timed_run(dk, sbid, [pid], dict(kn, plain_mode=1), plain_ligands, sat, so, sx, stream, torch)
-        sweep[key(kn)]["plain_ligands_per_s"] = plain_ligands / t
+        r = ck.get(f"plain_{plain_ligands}_{tag(key(kn))}", lambda kn=kn: dict(seconds=np.float64(_timed_run(
+            dk, sbid, [pid], dict(kn, plain_mode=1), plain_ligands, sat, so, sx, stream, torch))))
+        sweep[key(kn)]["plain_ligands_per_s"] = plain_ligands / float(r["seconds"])
     dk.release_batch(sbid)
     dk.release_batch(bid)
 
@@ -97,7 +129,8 @@ def run(ligands=100_000, fit_ligands=4_000, plain_ligands=128, seed=3, combos=No
         gl, gt = gb.sizes()
         for p_i, (fp, fpid) in enumerate(zip(fit_pockets, fpids)):
             for kn in combos:
-                secs = _timed_run(dk, gbid, [fpid], kn, gn, gat, go, gx, stream, torch)
+                secs = float(ck.get(f"fit_{fit_ligands}_{gi}_{p_i}_{tag(key(kn))}", lambda kn=kn, fpid=fpid: dict(
+                    seconds=np.float64(_timed_run(dk, gbid, [fpid], kn, gn, gat, go, gx, stream, torch))))["seconds"])
                 rows.append(dict(config=key(kn), pocket=p_i, group=gi, npts=len(fp.pts), mean_atoms=float(gl.mean()),
                                  mean_rot=float(gt.mean()), nu=gn, seconds=secs))
         dk.release_batch(gbid)
@@ -152,9 +185,11 @@ def main():
     ap.add_argument("--fit-ligands", type=int, default=4_000)
     ap.add_argument("--plain-ligands", type=int, default=128)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--checkpoint", default=None, help="directory of finished shards (resumes a stopped run)")
     args = ap.parse_args()
     t0 = time.time()
-    res = run(args.ligands, args.fit_ligands, args.plain_ligands, log=lambda *a: print(*a, file=sys.stderr))
+    res = run(args.ligands, args.fit_ligands, args.plain_ligands, log=lambda *a: print(*a, file=sys.stderr),
+              checkpoint=args.checkpoint)
     res["wall_s"] = time.time() - t0
     txt = json.dumps(res)
     if args.out:

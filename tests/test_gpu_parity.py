@@ -219,3 +219,33 @@ def test_exact_score_needs_probe_points(dk):
     r1, _ = dk.run(bid, [pid2], C.knobs(), b.n, _natoms(b))
     assert np.array_equal(r0.view(np.int32), r1.view(np.int32))
     dk.release_batch(bid)
+
+
+def test_autotune_picks_a_valid_shape_with_identical_results(dk):
+    pk = synth.pocket(8, 64, 0.5, C.ELLIPSOID)
+    l, t = synth.ligand_sizes(15, 96, 0, [16, 64, 2, 12])
+    b = synth.ligand_batch(15, l, t)
+    kn = C.knobs(n_poses=32, hp_step=10.0, lp_step=10.0, repetitions=1, seed=4)
+    pid = dk.init_pocket(pk)
+    bid = dk.upload_ligands(b)
+    ref, rx = dk.run(bid, [pid], kn, b.n, _natoms(b))
+    q, kc, w = dk.autotune(bid, pid, kn)
+    assert q in (1, 2, 4, 8) and kc in (8, 12, 18, 36) and w in (2, 4, 8)
+    res, xyz = dk.run(bid, [pid], kn, b.n, _natoms(b))  # now with the tuned shape
+    assert np.array_equal(res.view(np.int32), ref.view(np.int32)) and np.array_equal(xyz, rx)
+    dk.release_batch(bid)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_run_to_run_bitwise_determinism(dk, mode):
+    pk = synth.pocket(13, 48, 0.5, (6, 5, 4))
+    l, t = synth.ligand_sizes(16, 24, 0, [16, 40, 1, 8])
+    b = synth.ligand_batch(16, l, t)
+    kn = C.knobs(n_poses=20, hp_step=20.0, lp_step=20.0, repetitions=2, seed=6, score_mode=mode)
+    pid = dk.init_pocket(pk)
+    bid = dk.upload_ligands(b)
+    outs = [dk.run(bid, [pid], kn, b.n, _natoms(b)) for _ in range(3)]
+    for res, xyz in outs[1:]:
+        assert np.array_equal(res.view(np.int32), outs[0][0].view(np.int32))
+        assert np.array_equal(xyz, outs[0][1])
+    dk.release_batch(bid)
