@@ -1,19 +1,20 @@
 // Device code of the batched pose evaluator (GeoDock-MA, Alg. 1/2, Eq. 1).
 //
 // Work decomposition. A warp owns G = 32/Q initial poses of ONE ligand in ONE
-// pocket; Q lanes share a pose and split its candidate angles. Because every
-// pose of a warp has the same topology, loops over atoms, fragments and
-// angles are warp-uniform; only coordinates differ per lane. Coordinates of
-// the warp's poses live in shared memory as [atom][axis][pose] in grid units
-// of the pocket, shifted so that floor(t) is the nearest voxel.
+// pocket; the Q lanes of a pose split its moving atoms (and its fixed atoms
+// for the fixed part of the score). Because every pose of a warp has the same
+// topology, loops over atoms, fragments and angles are warp-uniform; only
+// coordinates differ per lane. Coordinates of the warp's poses live in shared
+// memory as [atom][axis][pose] in grid units of the pocket, shifted so that
+// floor(t) is the nearest voxel.
 //
 // Per fragment sweep (Alg. 1), with c the fragment's bond atom (on the axis)
-// and k the unit bond axis, every moving atom x is split once into
+// and k the unit bond axis, every moving atom x is split into
 //   a = c + k (k.(x-c)),  u = (x-c) - k (k.(x-c)),  w = k x u,
 // so the candidate at angle theta is a + cos(theta) u + sin(theta) w (Rodrigues'
 // formula). A lane keeps a chunk of KC angles' partial scores in registers
-// and walks the moving atoms once per chunk. The fixed atoms' part of the
-// score is summed once per sweep.
+// and walks its moving atoms once per chunk; the pose's lanes then add their
+// partial sums. The fixed atoms' part of the score is summed once per sweep.
 //
 // Score (Eq. 1): o = l / (h^2 S), S = sum_i K(voxel(x_i)) in grid units with K
 // the floored integer field, so S is an exact integer (nearest mode) and the
@@ -21,9 +22,11 @@
 // exact mode takes Eq. 1's inner minimum over the pocket points directly.
 //
 // Bump check (Alg. 1 "the ligand shape is feasible"): pairs (i in M\{c},
-// j in F\{b}). For atom i on its circle (centre a, radius r = |u|) and a fixed
-// atom y, |x(theta) - y| >= |a - y| - r, so a pair with |a - y| >= thr + r +
-// margin can never clash and is skipped; the rest are tested per angle with
+// j in F\{b}). Atom i moves on a circle of radius r about the axis at axial
+// position h; a fixed atom y at radius rho and axial position t comes no
+// closer than sqrt((rho - r)^2 + (t - h)^2), so a pair whose closest approach
+// exceeds the threshold (plus a margin for FP32 rounding) is skipped; the rest
+// are tested at every candidate with
 // d^2(theta) = |a-y|^2 + r^2 + cos(theta) 2(a-y).u + sin(theta) 2(a-y).w.
 #pragma once
 
