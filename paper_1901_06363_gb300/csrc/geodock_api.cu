@@ -220,9 +220,11 @@ dock_tile default_tile(const dock_knobs* k) {
 }
 
 // Shared-memory floats per warp for its poses' coordinates: 32 atoms of
-// 32 / lanes_per_pose poses (never more than the batch needs).
+// 32 / lanes_per_pose poses (never more than the batch needs), and at least
+// one pose of the batch's largest ligand (which then runs one pose per warp).
 int slice_floats(const dock_tile& t, int lmax) {
-    return ((32 / t.lanes_per_pose) * std::min(32, lmax) * 3 + 3) & ~3;  // 16-byte multiple
+    const int base = (32 / t.lanes_per_pose) * std::min(32, lmax) * 3;
+    return (std::max(base, 3 * lmax) + 3) & ~3;  // 16-byte multiple
 }
 
 // log2 of the lanes per pose for a ligand of l atoms: the smallest Q >= the

@@ -249,3 +249,12 @@ def test_run_to_run_bitwise_determinism(dk, mode):
         assert np.array_equal(res.view(np.int32), outs[0][0].view(np.int32))
         assert np.array_equal(xyz, outs[0][1])
     dk.release_batch(bid)
+
+
+def test_largest_ligands(dk):
+    """Ligands up to DOCK_MAX_ATOMS (255): more lanes per pose so their poses fit a warp's slice."""
+    pk = synth.pocket(8, 96, 0.5, (11, 9, 7))
+    b = synth.ligand_batch(7, np.array([255, 200, 120, 33]), np.array([6, 5, 4, 3]))
+    kn = C.knobs(n_poses=6, hp_step=30.0, lp_step=30.0, repetitions=1, seed=8, clip_box=0)
+    stats, g, res = trace_parity(dk, pk, b, kn)
+    assert stats["candidates"] > 500
