@@ -258,3 +258,25 @@ def test_largest_ligands(dk):
     kn = C.knobs(n_poses=6, hp_step=30.0, lp_step=30.0, repetitions=1, seed=8, clip_box=0)
     stats, g, res = trace_parity(dk, pk, b, kn)
     assert stats["candidates"] > 500
+
+
+@pytest.mark.parametrize("case", ["step1", "step1_peel", "step7", "thr0", "poses4096", "tiny_rotor"])
+def test_stress_cases(dk, case):
+    pk = synth.pocket(13, 64, 0.5, (6, 5, 4))
+    if case == "tiny_rotor":
+        # four atoms in a chain with its middle bond rotatable: one moving atom per side
+        x = np.array([[0, 0, 0], [1.5, 0, 0], [2.0, 1.4, 0], [3.5, 1.4, 0.3]], np.float32)
+        b = synth.LigandBatch([0, 4], [0, 3], [0, 1], x, np.array([[0, 1], [1, 2], [2, 3]], np.int32),
+                              np.array([1], np.int32))
+    else:
+        l, t = synth.ligand_sizes(17, 3 if case == "poses4096" else 5, 0, [16, 40, 2, 6])
+        b = synth.ligand_batch(17, l, t)
+    kn = {
+        "step1": C.knobs(n_poses=3, hp_step=1.0, lp_step=1.0, repetitions=1, seed=2),
+        "step1_peel": C.knobs(n_poses=3, hp_step=1.0, lp_step=30.0, threshold=0.2, enable_refinement=1, seed=7),
+        "step7": C.knobs(n_poses=5, hp_step=7.0, lp_step=20.0, threshold=0.3, seed=3),
+        "thr0": C.knobs(n_poses=9, bump_thr=0.0, repetitions=2, seed=4),
+        "poses4096": C.knobs(n_poses=4096, hp_step=45.0, lp_step=45.0, repetitions=1, seed=5),
+        "tiny_rotor": C.knobs(n_poses=16, hp_step=10.0, lp_step=10.0, repetitions=2, seed=6),
+    }[case]
+    trace_parity(dk, pk, b, kn)
