@@ -211,7 +211,7 @@ def run_ours(args):
         total_s = float(t.item())
         dist.barrier()
     st = dk.stats()
-    cand_per_step = st["candidates"]
+    cand_per_step = st["candidates"]  # evaluated candidates (repetitions left out at a fixed point excluded)
     value = world * n * args.steps / total_s
 
     if args.no_baselines:
@@ -330,6 +330,7 @@ def run_ours(args):
         "e2e": e2e,
         "clocks": clocks,
         "gpu_launches": int(st["kernel_launches"]) * args.steps,
+        "pose_reps_skipped_per_step": int(st["pose_reps_skipped"]),
     }
     print(json.dumps(line), flush=True)
     if dist:

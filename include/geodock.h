@@ -256,7 +256,11 @@ int dock_autotune(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs* 
  *   kernel_launches  CUDA kernels launched by the call
  *   sweep_ms         device time of the sweep kernel(s) of the call, from
  *                    CUDA events recorded around them on the call's stream
- *                    (waits for the call to finish) */
+ *                    (waits for the call to finish)
+ *   pose_reps_skipped  (pose, repetition) pairs not computed: when a whole
+ *                    repetition moves no pose of a warp, each further
+ *                    repetition would repeat it exactly, so the warp stops;
+ *                    the counts above exclude that work */
 typedef struct {
     uint64_t candidates;
     uint64_t atom_updates;
@@ -264,6 +268,7 @@ typedef struct {
     uint64_t bump_pairs;
     uint64_t kernel_launches;
     double sweep_ms;
+    uint64_t pose_reps_skipped;
 } dock_stats;
 
 int dock_last_stats(const dock_ctx* ctx, dock_stats* s);

@@ -84,6 +84,7 @@ struct Plan {
     int ntask = 0, npairs = 0, slice = 0;
     std::vector<int> task_off;  // first task of each pair (plain form: pair order)
     std::unique_ptr<DevBuf> tasks, pockets, cs_hp, cs_lp, cs_peel;
+    std::unique_ptr<DevBuf> skipped;  // per pair: pose-repetitions left out at a fixed point
     SweepParams P{};
     FinalParams F{};
     int kc = 12, Q = 1, W = 4, grid = 1, block = 128;
@@ -96,6 +97,16 @@ struct Plan {
 };
 
 }  // namespace
+
+// Work of one repetition of one pose per ligand (from the topology and knobs)
+// and the device counts of pose-repetitions the last run left out at a fixed
+// point; dock_last_stats subtracts that work.
+struct WorkTally {
+    std::vector<uint64_t> cand, upd, bounds, pairs;
+    int nlig = 0, npairs = 0;
+    DevBuf* skipped = nullptr;
+    bool pending = false;
+};
 
 struct dock_ctx {
     int device = 0;
@@ -112,6 +123,7 @@ struct dock_ctx {
     std::map<std::string, std::unique_ptr<DevBuf>> pocket_sets;  // device pocket arrays per pocket list
     std::map<std::string, std::unique_ptr<Plan>> plans;
     dock_stats stats{};
+    WorkTally tally;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the sweep kernel(s) of the last run
     bool timed = false;
     ~dock_ctx() {
@@ -759,6 +771,28 @@ int dock_last_stats(const dock_ctx* ctx_, dock_stats* s) {
         ctx->stats.sweep_ms = ms;
         ctx->timed = false;
     }
+    WorkTally& W = ctx->tally;
+    if (W.pending && W.skipped && W.npairs > 0) {
+        // repetitions left out at a fixed point were not computed: count only the work done
+        std::vector<unsigned> sk(W.npairs);
+        CK(cudaDeviceSynchronize());
+        CK(cudaMemcpy(sk.data(), W.skipped->p, (size_t)W.npairs * sizeof(unsigned), cudaMemcpyDeviceToHost));
+        uint64_t reps = 0, c = 0, u = 0, bd = 0, pr = 0;
+        for (int pair = 0; pair < W.npairs; ++pair) {
+            const int b = pair % W.nlig;
+            reps += sk[pair];
+            c += sk[pair] * W.cand[b];
+            u += sk[pair] * W.upd[b];
+            bd += sk[pair] * W.bounds[b];
+            pr += sk[pair] * W.pairs[b];
+        }
+        ctx->stats.pose_reps_skipped = reps;
+        ctx->stats.candidates -= c;
+        ctx->stats.atom_updates -= u;
+        ctx->stats.pair_bounds -= bd;
+        ctx->stats.bump_pairs -= pr;
+        W.pending = false;
+    }
     *s = ctx->stats;
     return DOCK_OK;
 }
@@ -899,6 +933,9 @@ int get_plan(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const doc
     P.per_tile = per_tile;
     P.pose_key = ctx->pose_key.as<unsigned long long>();
     P.pose_xyz = ctx->pose_xyz.as<float>();
+    pl->skipped.reset(new DevBuf());
+    CK(pl->skipped->ensure((size_t)std::max(1, pl->npairs) * sizeof(unsigned)));
+    P.skipped = pl->skipped->as<unsigned>();
     P.trace_on = 0;
     P.bw = bump_words(k);
     pl->smem = cta_smem(t, pl->slice, P.bw);
@@ -928,6 +965,7 @@ int get_plan(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const doc
 // Enqueue one batched run: reset the queue, persistent sweep, finalize.
 int enqueue_batched(dock_ctx* ctx, Plan* pl, const dock_knobs* k, cudaStream_t s) {
     CK(cudaMemsetAsync(ctx->counter.p, 0, sizeof(unsigned), s));
+    CK(cudaMemsetAsync(pl->skipped->p, 0, (size_t)std::max(1, pl->npairs) * sizeof(unsigned), s));
     // external event records become event nodes when this is captured into a graph; outside a
     // capture (the autotuner) they are plain records
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -946,6 +984,7 @@ int enqueue_batched(dock_ctx* ctx, Plan* pl, const dock_knobs* k, cudaStream_t s
 // Plain comparison form: per (pocket, ligand) pair, its own queue reset,
 // sweep launch over that pair's pose groups, and finalize launch.
 int enqueue_plain(dock_ctx* ctx, Plan* pl, const dock_knobs* k, cudaStream_t s) {
+    CK(cudaMemsetAsync(pl->skipped->p, 0, (size_t)std::max(1, pl->npairs) * sizeof(unsigned), s));
     CK(cudaEventRecord(ctx->ev0, s));
     for (int pair = 0; pair < pl->npairs; ++pair) {
         SweepParams P = pl->P;
@@ -987,7 +1026,13 @@ int check_run_args(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, con
 void count_work(dock_ctx* ctx, const BatchH& B, int np, const dock_knobs* k, const Plan* pl, uint64_t launches) {
     int P_hp = n_angles(k->hp_step), P_lp = n_angles(k->lp_step);
     uint64_t cand = 0, upd = 0, bounds = 0, pairs = 0;
-    for (int b = 0; b < B.n; ++b)
+    WorkTally& W = ctx->tally;
+    W.cand.assign(B.n, 0);
+    W.upd.assign(B.n, 0);
+    W.bounds.assign(B.n, 0);
+    W.pairs.assign(B.n, 0);
+    for (int b = 0; b < B.n; ++b) {
+        const uint64_t c0 = cand, u0 = upd, b0 = bounds, p0 = pairs;
         for (int s = 0; s < B.nside[b]; ++s) {
             int si = B.side_off[b] + s;
             bool coarse = (double)B.side_m[si] / (double)B.l[b] <= k->threshold;
@@ -1004,6 +1049,16 @@ void count_work(dock_ctx* ctx, const BatchH& B, int np, const dock_knobs* k, con
             // the circle bound tests every pair once per sweep
             bounds += (uint64_t)B.side_nmov[si] * B.side_nfixB[si];
         }
+        // one repetition of one pose of ligand b
+        W.cand[b] = cand - c0;
+        W.upd[b] = upd - u0;
+        W.bounds[b] = bounds - b0;
+        W.pairs[b] = pairs - p0;
+    }
+    W.nlig = B.n;
+    W.npairs = np * B.n;
+    W.skipped = pl ? pl->skipped.get() : nullptr;
+    W.pending = W.skipped != nullptr;
     uint64_t mult = (uint64_t)np * k->n_poses * k->repetitions;
     ctx->stats.candidates = cand * mult;
     ctx->stats.atom_updates = upd * mult;
@@ -1011,6 +1066,7 @@ void count_work(dock_ctx* ctx, const BatchH& B, int np, const dock_knobs* k, con
     ctx->stats.bump_pairs = pairs * mult;
     ctx->stats.kernel_launches = launches;
     ctx->stats.sweep_ms = -1.0;
+    ctx->stats.pose_reps_skipped = 0;
     ctx->timed = true;
 }
 

@@ -114,6 +114,7 @@ struct SweepParams {
     int per_tile;        // tile / hp_step
     // per-pose results (scratch)
     unsigned long long* pose_key;  // (float bits of S) << 32 | pose; ~0 when skipped
+    unsigned* skipped;             // per pair: pose-repetitions left out at a fixed point (nullable)
     float* pose_xyz;               // grid units, ((pocket*natoms + atom_off)*N + p*l + i)*3
     int trace_on;
     TraceDev tr;
@@ -539,6 +540,7 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
 
         if (__any_sync(FULL, live)) {
             for (int rep = 0; rep < P.repetitions; ++rep) {
+                bool moved = false;  // did this pose commit any angle in this repetition
                 for (int si = 0; si < L.nside; ++si) {
                     const SideDev sd = P.side[L.side_off + si];
                     const int sweep = rep * L.nside + si;
@@ -805,7 +807,16 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                         S_inc = __uint_as_float((unsigned)(best >> 32));
                     }
                     if (P.trace_on && active && q == 0) P.tr.chosen_k[tbase + sweep] = kb;
+                    moved = moved || kb != 0;
                     __syncwarp();
+                }
+                // a repetition in which no pose of the warp moved left every pose where it was, so
+                // each further repetition would repeat it exactly: stop (the trace records them all)
+                if (!P.trace_on && !__any_sync(FULL, moved)) {
+                    const unsigned poses = __popc(__ballot_sync(FULL, active && q == 0));
+                    if (P.skipped && lane == 0 && rep + 1 < P.repetitions)
+                        atomicAdd(P.skipped + tk.x, poses * (unsigned)(P.repetitions - 1 - rep));
+                    break;
                 }
             }
         }

@@ -280,3 +280,27 @@ def test_stress_cases(dk, case):
         "tiny_rotor": C.knobs(n_poses=16, hp_step=10.0, lp_step=10.0, repetitions=2, seed=6),
     }[case]
     trace_parity(dk, pk, b, kn)
+
+
+def test_fixed_point_repetitions_are_counted_out(dk):
+    """Repetitions after one that moved no pose of a warp are not computed; the work counts exclude them
+    and the results equal the traced run, which computes every repetition."""
+    pk = synth.pocket(8, 64, 0.5, C.ELLIPSOID)
+    l, t = synth.ligand_sizes(18, 12, 0, [16, 40, 1, 6])
+    b = synth.ligand_batch(18, l, t)
+    kn = C.knobs(n_poses=16, hp_step=30.0, lp_step=30.0, repetitions=8, seed=9)
+    pid = dk.init_pocket(pk)
+    bid = dk.upload_ligands(b)
+    res, _ = dk.run(bid, [pid], kn, b.n, _natoms(b))
+    st = dk.stats()
+    full = 0
+    for i in range(b.n):
+        lb = int(b.atom_off[i + 1] - b.atom_off[i])
+        tb = int(b.rot_off[i + 1] - b.rot_off[i])
+        full += 2 * tb * (oracle.n_angles(30.0) - 1)
+    full *= kn["n_poses"] * kn["repetitions"]
+    assert st["pose_reps_skipped"] > 0
+    assert 0 < st["candidates"] < full
+    g = dk.run_trace(bid, pid, kn, b)
+    assert np.array_equal(res.view(np.int32), g["result"].view(np.int32))
+    dk.release_batch(bid)
