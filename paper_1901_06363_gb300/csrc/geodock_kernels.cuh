@@ -538,9 +538,15 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
             }
         }
 
+        // A pose whose last repetition committed no angle is at a fixed point: every further sweep
+        // keeps its incumbent, so its sweeps are not computed (except when tracing); a warp
+        // whose poses are all at a fixed point stops. nskip counts the pose-repetitions left out.
+        bool conv = false;
+        unsigned nskip = 0;
         if (__any_sync(FULL, live)) {
             for (int rep = 0; rep < P.repetitions; ++rep) {
                 bool moved = false;  // did this pose commit any angle in this repetition
+                const bool work = live && !conv;
                 for (int si = 0; si < L.nside; ++si) {
                     const SideDev sd = P.side[L.side_off + si];
                     const int sweep = rep * L.nside + si;
@@ -661,8 +667,8 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                                             if (fmaf(dr1, dr1, dh1 * dh1) < lim) near1 |= 1u << j;
                                         }
                                     }
-                                    if (!live || !have_tile) near0 = 0;
-                                    if (!live || !have_tile || f1 == f) near1 = 0;
+                                    if (!work || !have_tile) near0 = 0;
+                                    if (!work || !have_tile || f1 == f) near1 = 0;
                                     unsigned long long pairs = near0 | ((unsigned long long)near1 << 8);
                                     while (pairs) {
                                         const int e = __ffsll(pairs) - 1;
@@ -716,7 +722,7 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                                 uint64_t b0 = col[w * 32] >> sh;
                                 if (sh + KC > 64 && w + 1 < P.bw) b0 |= col[(w + 1) * 32] << (64 - sh);
                                 b0 = group_or(b0, Q);
-                                uint64_t nd = (live && have_tile) ? ~b0 : 0ull;
+                                uint64_t nd = (work && have_tile) ? ~b0 : 0ull;
                                 nd &= nvalid >= 64 ? ~0ull : ((1ull << nvalid) - 1ull);
                                 const unsigned lo = __reduce_or_sync(FULL, (unsigned)nd);
                                 const unsigned hi = __reduce_or_sync(FULL, (unsigned)(nd >> 32));
@@ -792,7 +798,7 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                             best = pbest < best ? pbest : best;
                         }
                     }
-                    const int kb = live ? (int)(best & 0xffffffffu) : 0;
+                    const int kb = work ? (int)(best & 0xffffffffu) : 0;
                     if (kb != 0) {
                         // the same rotation as the candidate's evaluation
                         const float2 v = !peel ? cs[kb] : P.cs_hp[kb - 1 - P.n_tiles];
@@ -812,13 +818,18 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                 }
                 // a repetition in which no pose of the warp moved left every pose where it was, so
                 // each further repetition would repeat it exactly: stop (the trace records them all)
+                if (conv && active && q == 0) ++nskip;
+                if (!P.trace_on && !moved) conv = true;
                 if (!P.trace_on && !__any_sync(FULL, moved)) {
-                    const unsigned poses = __popc(__ballot_sync(FULL, active && q == 0));
-                    if (P.skipped && lane == 0 && rep + 1 < P.repetitions)
-                        atomicAdd(P.skipped + tk.x, poses * (unsigned)(P.repetitions - 1 - rep));
+                    if (active && q == 0) nskip += (unsigned)(P.repetitions - 1 - rep);
                     break;
                 }
             }
+        }
+        if (P.skipped) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) nskip += __shfl_xor_sync(FULL, nskip, o);
+            if (lane == 0 && nskip) atomicAdd(P.skipped + tk.x, nskip);
         }
         // ---- per-pose result
         if (active && q == 0) {
