@@ -257,10 +257,11 @@ int dock_autotune(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs* 
  *   sweep_ms         device time of the sweep kernel(s) of the call, from
  *                    CUDA events recorded around them on the call's stream
  *                    (waits for the call to finish)
- *   pose_reps_skipped  (pose, repetition) pairs not computed: when a whole
- *                    repetition moves no pose of a warp, each further
- *                    repetition would repeat it exactly, so the warp stops;
- *                    the counts above exclude that work */
+ *   pose_reps_skipped  (pose, repetition) pairs not computed: a repetition
+ *                    that commits no angle for a pose leaves it where it
+ *                    was, so each further repetition would repeat it
+ *                    exactly; a pose that starts outside the box (clip_box)
+ *                    computes none; the counts above exclude that work */
 typedef struct {
     uint64_t candidates;
     uint64_t atom_updates;

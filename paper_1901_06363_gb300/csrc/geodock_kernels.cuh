@@ -540,8 +540,9 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
 
         // A pose whose last repetition committed no angle is at a fixed point: every further sweep
         // keeps its incumbent, so its sweeps are not computed (except when tracing); a warp
-        // whose poses are all at a fixed point stops. nskip counts the pose-repetitions left out.
-        bool conv = false;
+        // whose poses are all at a fixed point stops. nskip counts the pose-repetitions left out; a
+        // pose that starts outside the box computes none.
+        bool conv = !live;
         unsigned nskip = 0;
         if (__any_sync(FULL, live)) {
             for (int rep = 0; rep < P.repetitions; ++rep) {
@@ -825,6 +826,8 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                     break;
                 }
             }
+        } else if (active && q == 0) {
+            nskip = (unsigned)P.repetitions;
         }
         if (P.skipped) {
 #pragma unroll

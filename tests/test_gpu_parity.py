@@ -282,10 +282,12 @@ def test_stress_cases(dk, case):
     trace_parity(dk, pk, b, kn)
 
 
-def test_fixed_point_repetitions_are_counted_out(dk):
-    """Repetitions after one that moved no pose of a warp are not computed; the work counts exclude them
-    and the results equal the traced run, which computes every repetition."""
-    pk = synth.pocket(8, 64, 0.5, C.ELLIPSOID)
+@pytest.mark.parametrize("n_grid", [64, 16])
+def test_fixed_point_repetitions_are_counted_out(dk, n_grid):
+    """Repetitions after one that committed no angle for a pose are not computed; the work counts
+    exclude them and the results equal the traced run, which computes every repetition. On the 16^3
+    grid many poses start outside the box and compute nothing."""
+    pk = synth.pocket(8, n_grid, 0.5, C.ELLIPSOID)
     l, t = synth.ligand_sizes(18, 12, 0, [16, 40, 1, 6])
     b = synth.ligand_batch(18, l, t)
     kn = C.knobs(n_poses=16, hp_step=30.0, lp_step=30.0, repetitions=8, seed=9)
@@ -303,4 +305,24 @@ def test_fixed_point_repetitions_are_counted_out(dk):
     assert 0 < st["candidates"] < full
     g = dk.run_trace(bid, pid, kn, b)
     assert np.array_equal(res.view(np.int32), g["result"].view(np.int32))
+    # the traced run computes every repetition: from its chosen angles, a pose stops after its first
+    # repetition that commits none (a pose outside the box computes none); count what is left out
+    N, R = kn["n_poses"], kn["repetitions"]
+    skipped, left_out, side_off = 0, 0, 0
+    for i in range(b.n):
+        ns = 2 * int(b.rot_off[i + 1] - b.rot_off[i])
+        for p in range(N):
+            if g["pose_status"][i * N + p] != 0:
+                n = R
+            else:
+                ck = g["chosen_k"][N * R * side_off + p * R * ns:][:R * ns].reshape(R, ns)
+                still = np.flatnonzero((ck == 0).all(axis=1))
+                n = R - 1 - int(still[0]) if len(still) else 0
+            skipped += n
+            left_out += n * ns * (oracle.n_angles(30.0) - 1)
+        side_off += ns
+    assert st["pose_reps_skipped"] == skipped
+    assert st["candidates"] == full - left_out
+    if n_grid == 16:
+        assert (g["pose_status"][:b.n * N] != 0).any()
     dk.release_batch(bid)
