@@ -171,6 +171,15 @@ __device__ __forceinline__ float3 place(const Split& s, float cs, float sn) {
                        __fmaf_rn(sn, s.w.z, __fmaf_rn(cs, s.u.z, s.a.z)));
 }
 
+// Angle tables in shared memory are paired: entry p holds (cos, cos, sin, sin)
+// of angles 2p and 2p+1, so two candidates' coordinates come from one packed
+// FP32 multiply-add (the same rounding as two fmaf) per axis and term.
+__device__ __forceinline__ float2 angle_at(const float4* t, int j) {
+    const float4 v = t[j >> 1];
+    return (j & 1) ? make_float2(v.y, v.w) : make_float2(v.x, v.z);
+}
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+
 // Eq. 1's inner minimum taken over the probe points themselves, at grid
 // position t shifted by +0.5 (points stored shifted alike), floored at 1.
 __device__ __forceinline__ float exact_min(const PocketDev& pd, float3 t) {
@@ -366,35 +375,55 @@ __device__ __forceinline__ float outside2(const PocketDev& pd, float3 t) {
 // the lookup is clamped and the squared distance outside goes to pen.
 template <int KC, int MODE, bool CLIP, int NA>
 __device__ __forceinline__ void score_atoms(const PocketDev& pd, const uint16_t* __restrict__ K, uint32_t bias,
-                                            const Split (&s)[NA], bool fast, const float2* __restrict__ cst,
+                                            const Split (&s)[NA], bool fast, const float4* __restrict__ cst,
                                             typename Acc<MODE>::T (&acc)[KC], float (&pen)[KC], uint64_t& box,
                                             uint64_t need) {
     if (MODE == 0 && fast) {
-        // padded field: circle centres moved by PAD voxels; outside values sum past OUTSIDE
-        Split sp[NA];
+        // padded field: circle centres moved by PAD voxels; outside values sum past OUTSIDE.
+        // Candidates two at a time: packed multiply-adds place both, packed adds floor both.
+        float2 ax[NA], ay[NA], az[NA], ux[NA], uy[NA], uz[NA], wx[NA], wy[NA], wz[NA];
 #pragma unroll
         for (int a = 0; a < NA; ++a) {
-            sp[a] = s[a];
-            sp[a].a = make_float3(s[a].a.x + (float)PAD, s[a].a.y + (float)PAD, s[a].a.z + (float)PAD);
+            ax[a] = dup2(s[a].a.x + (float)PAD);
+            ay[a] = dup2(s[a].a.y + (float)PAD);
+            az[a] = dup2(s[a].a.z + (float)PAD);
+            ux[a] = dup2(s[a].u.x);
+            uy[a] = dup2(s[a].u.y);
+            uz[a] = dup2(s[a].u.z);
+            wx[a] = dup2(s[a].w.x);
+            wy[a] = dup2(s[a].w.y);
+            wz[a] = dup2(s[a].w.z);
         }
         const uint32_t pnx = (uint32_t)(pd.nx + 2 * PAD), pny = (uint32_t)(pd.ny + 2 * PAD);
+        const float2 magic = dup2(8388608.0f);
         // blocks of candidates that no pose of the warp needs (all infeasible) are skipped
         constexpr int BLK = KC % 6 == 0 ? 6 : 4;
+        static_assert(KC % 2 == 0 && BLK % 2 == 0, "candidates go in pairs");
 #pragma unroll
         for (int jb = 0; jb < KC; jb += BLK) {
             if ((need >> jb) & ((1ull << BLK) - 1ull)) {
 #pragma unroll
-                for (int j = jb; j < jb + BLK && j < KC; ++j) {
-                    const float2 c = cst[j];
+                for (int j = jb; j < jb + BLK && j < KC; j += 2) {
+                    const float4 cc = cst[j >> 1];
+                    const float2 c2 = make_float2(cc.x, cc.y), s2 = make_float2(cc.z, cc.w);
 #pragma unroll
-                    for (int a = 0; a < NA; ++a) acc[j] += lookup_padded(pd.Kp, pnx, pny, bias, place(sp[a], c.x, c.y));
+                    for (int a = 0; a < NA; ++a) {
+                        // a + cos u + sin w, then the round-toward-zero add that floors (as in lookup_padded)
+                        const float2 bx = __fadd2_rz(__ffma2_rn(s2, wx[a], __ffma2_rn(c2, ux[a], ax[a])), magic);
+                        const float2 by = __fadd2_rz(__ffma2_rn(s2, wy[a], __ffma2_rn(c2, uy[a], ay[a])), magic);
+                        const float2 bz = __fadd2_rz(__ffma2_rn(s2, wz[a], __ffma2_rn(c2, uz[a], az[a])), magic);
+                        acc[j] += __ldg(pd.Kp + (__float_as_uint(bx.x) +
+                                                 pnx * (__float_as_uint(by.x) + pny * __float_as_uint(bz.x)) - bias));
+                        acc[j + 1] += __ldg(pd.Kp + (__float_as_uint(bx.y) +
+                                                     pnx * (__float_as_uint(by.y) + pny * __float_as_uint(bz.y)) - bias));
+                    }
                 }
             }
         }
     } else if (MODE == 0) {
 #pragma unroll
         for (int j = 0; j < KC; ++j) {
-            const float2 c = cst[j];
+            const float2 c = angle_at(cst, j);
 #pragma unroll
             for (int a = 0; a < NA; ++a) {
                 const float3 t = place(s[a], c.x, c.y);
@@ -414,7 +443,8 @@ __device__ __forceinline__ void score_atoms(const PocketDev& pd, const uint16_t*
             float m[KC];
 #pragma unroll
             for (int j = 0; j < KC; ++j) {
-                t[j] = place(s[a], cst[j].x, cst[j].y);
+                const float2 c = angle_at(cst, j);
+                t[j] = place(s[a], c.x, c.y);
                 m[j] = 3.0e38f;
             }
             for (int p = 0; p < pd.npts; ++p) {
@@ -436,7 +466,7 @@ __device__ __forceinline__ void score_atoms(const PocketDev& pd, const uint16_t*
     } else {
 #pragma unroll
         for (int j = 0; j < KC; ++j) {
-            const float2 c = cst[j];
+            const float2 c = angle_at(cst, j);
 #pragma unroll
             for (int a = 0; a < NA; ++a) {
                 bool in;
@@ -455,7 +485,7 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
     const int warp = threadIdx.x >> 5;
     float* xs = smem + (size_t)warp * (P.slice + warp_extra_floats(KC, P.bw));
     unsigned long long* bump = reinterpret_cast<unsigned long long*>(xs + P.slice);  // [bw][32]
-    float2* ptab = reinterpret_cast<float2*>(xs + P.slice + P.bw * 64);             // the phase's (cos, sin)
+    float2* ptab = reinterpret_cast<float2*>(xs + P.slice + P.bw * 64);             // the phase's angles, paired
     uint8_t* sidx = reinterpret_cast<uint8_t*>(ptab + 64 * P.bw + ptab_pad(KC));    // the sweep's index lists
     unsigned long long* col = bump + lane;
     const float shift = MODE == 1 ? 0.0f : 0.5f;
@@ -628,8 +658,12 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                         for (int w = 0; w < nw; ++w) col[w * 32] = 0ull;
                         // the phase's angles, the same for every lane; (1, 0) past the end
                         __syncwarp();
-                        for (int j = lane; j < 64 * P.bw + ptab_pad(KC); j += 32)
-                            ptab[j] = j < ncand ? tab[j] : make_float2(1.f, 0.f);
+                        for (int j = lane; j < 64 * P.bw + ptab_pad(KC); j += 32) {
+                            const float2 v = j < ncand ? tab[j] : make_float2(1.f, 0.f);
+                            float* e = reinterpret_cast<float*>(ptab) + 4 * (j >> 1) + (j & 1);
+                            e[0] = v.x;
+                            e[2] = v.y;
+                        }
                         __syncwarp();
                         {
                             const float lim = thr2 + 0.05f;  // margin over the FP32 error of the bound
@@ -683,15 +717,19 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                                                         (sp.u.x * sp.u.x + sp.u.y * sp.u.y + sp.u.z * sp.u.z);
                                         const float B = 2.f * (dx * sp.u.x + dy * sp.u.y + dz * sp.u.z);
                                         const float C = 2.f * (dx * sp.w.x + dy * sp.w.y + dz * sp.w.z);
-                                        // candidates 12 at a time; a block may straddle two 64-bit words
+                                        // candidates 12 at a time, two per packed multiply-add; a block
+                                        // may straddle two 64-bit words
                                         const float4* tw = reinterpret_cast<const float4*>(ptab);
+                                        const float2 A2 = dup2(A), B2 = dup2(B), C2 = dup2(C);
                                         for (int g = 0; g < ncand; g += 12) {
                                             unsigned m12 = 0;
 #pragma unroll
                                             for (int k = 0; k < 6; ++k) {
                                                 const float4 t = tw[(g >> 1) + k];
-                                                if (fmaf(C, t.y, fmaf(B, t.x, A)) < thr2) m12 |= 1u << (2 * k);
-                                                if (fmaf(C, t.w, fmaf(B, t.z, A)) < thr2) m12 |= 2u << (2 * k);
+                                                const float2 d2 = __ffma2_rn(C2, make_float2(t.z, t.w),
+                                                                             __ffma2_rn(B2, make_float2(t.x, t.y), A2));
+                                                if (d2.x < thr2) m12 |= 1u << (2 * k);
+                                                if (d2.y < thr2) m12 |= 2u << (2 * k);
                                             }
                                             const int w = g >> 6, sh = g & 63;
                                             col[w * 32] |= (unsigned long long)m12 << sh;
@@ -707,7 +745,7 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                         for (int j0 = 0; j0 < ncand; j0 += KC) {
                             // the chunk's angles are the same for every lane of the warp
                             const int nvalid = min(KC, ncand - j0);
-                            const float2* cst = ptab + j0;
+                            const float4* cst = reinterpret_cast<const float4*>(ptab) + (j0 >> 1);
                             AT acc[KC];
                             float pen[KC];
 #pragma unroll
