@@ -51,10 +51,21 @@ struct DevBuf {
     T* as() const { return static_cast<T*>(p); }
 };
 
+// The padded field as a 3D texture (CUDA array, point sampling).
+struct FieldTex {
+    cudaArray_t arr = nullptr;
+    cudaTextureObject_t tex = 0;
+    ~FieldTex() {
+        if (tex) cudaDestroyTextureObject(tex);
+        if (arr) cudaFreeArray(arr);
+    }
+};
+
 struct PocketH {
     bool live = false;
     PocketDev d{};
     std::unique_ptr<DevBuf> K, Kp;
+    std::unique_ptr<FieldTex> Kt;
     std::unique_ptr<DevBuf> dev;  // device copy of d
     std::unique_ptr<DevBuf> pts;  // probe points for the exact score (float4, voxel + 0.5)
 };
@@ -569,6 +580,27 @@ int dock_init_pocket(dock_ctx* ctx, const dock_pocket* p, int* pocket_id) {
                                                                 p->ny, p->nz);
         CK(cudaGetLastError());
         CK(cudaDeviceSynchronize());
+        // and as a texture: point sampling at unnormalized coordinates returns the voxel at the floor
+        // of each coordinate (the same voxel as the padded lookups), from a cache-friendly 3D layout
+        const size_t ex = (size_t)(p->nx + 2 * PAD), ey = (size_t)(p->ny + 2 * PAD), ez = (size_t)(p->nz + 2 * PAD);
+        ph.Kt.reset(new FieldTex());
+        cudaChannelFormatDesc fd = cudaCreateChannelDesc<unsigned>();
+        CK(cudaMalloc3DArray(&ph.Kt->arr, &fd, make_cudaExtent(ex, ey, ez)));
+        cudaMemcpy3DParms cp = {};
+        cp.srcPtr = make_cudaPitchedPtr(ph.Kp->p, ex * sizeof(uint32_t), ex, ey);
+        cp.dstArray = ph.Kt->arr;
+        cp.extent = make_cudaExtent(ex, ey, ez);
+        cp.kind = cudaMemcpyDeviceToDevice;
+        CK(cudaMemcpy3D(&cp));
+        cudaResourceDesc rd = {};
+        rd.resType = cudaResourceTypeArray;
+        rd.res.array.array = ph.Kt->arr;
+        cudaTextureDesc td = {};
+        td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
+        td.filterMode = cudaFilterModePoint;
+        td.readMode = cudaReadModeElementType;
+        td.normalizedCoords = 0;
+        CK(cudaCreateTextureObject(&ph.Kt->tex, &rd, &td, nullptr));
     }
     // probe points for the exact score (Eq. 1's inner minimum without the grid)
     if (p->pts && p->npts > 0) {
@@ -587,6 +619,7 @@ int dock_init_pocket(dock_ctx* ctx, const dock_pocket* p, int* pocket_id) {
     }
     ph.d.K = ph.K->as<uint16_t>();
     ph.d.Kp = ph.Kp->as<uint32_t>();
+    ph.d.Kt = ph.Kt->tex;
     ph.d.nx = p->nx;
     ph.d.ny = p->ny;
     ph.d.nz = p->nz;

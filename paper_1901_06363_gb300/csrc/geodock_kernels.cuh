@@ -47,6 +47,8 @@ constexpr uint32_t OUTSIDE = 1u << 24;
 struct PocketDev {
     const uint16_t* K;   // floored field, x fastest
     const uint32_t* Kp;  // the same values padded by PAD voxels per side, OUTSIDE beyond the grid
+    unsigned long long Kt;  // Kp as a 3D texture (point sampling, unnormalized coordinates): a fetch at
+                            // padded position t returns Kp at floor(t)
     const float4* pts;   // probe points (voxel index + 0.5, grid units) for the exact score; NULL if unknown
     int npts;
     int nx, ny, nz;
@@ -394,8 +396,6 @@ __device__ __forceinline__ void score_atoms(const PocketDev& pd, const uint16_t*
             wy[a] = dup2(s[a].w.y);
             wz[a] = dup2(s[a].w.z);
         }
-        const uint32_t pnx = (uint32_t)(pd.nx + 2 * PAD), pny = (uint32_t)(pd.ny + 2 * PAD);
-        const float2 magic = dup2(8388608.0f);
         // blocks of candidates that no pose of the warp needs (all infeasible) are skipped
         constexpr int BLK = KC % 6 == 0 ? 6 : 4;
         static_assert(KC % 2 == 0 && BLK % 2 == 0, "candidates go in pairs");
@@ -408,14 +408,12 @@ __device__ __forceinline__ void score_atoms(const PocketDev& pd, const uint16_t*
                     const float2 c2 = make_float2(cc.x, cc.y), s2 = make_float2(cc.z, cc.w);
 #pragma unroll
                     for (int a = 0; a < NA; ++a) {
-                        // a + cos u + sin w, then the round-toward-zero add that floors (as in lookup_padded)
-                        const float2 bx = __fadd2_rz(__ffma2_rn(s2, wx[a], __ffma2_rn(c2, ux[a], ax[a])), magic);
-                        const float2 by = __fadd2_rz(__ffma2_rn(s2, wy[a], __ffma2_rn(c2, uy[a], ay[a])), magic);
-                        const float2 bz = __fadd2_rz(__ffma2_rn(s2, wz[a], __ffma2_rn(c2, uz[a], az[a])), magic);
-                        acc[j] += __ldg(pd.Kp + (__float_as_uint(bx.x) +
-                                                 pnx * (__float_as_uint(by.x) + pny * __float_as_uint(bz.x)) - bias));
-                        acc[j + 1] += __ldg(pd.Kp + (__float_as_uint(bx.y) +
-                                                     pnx * (__float_as_uint(by.y) + pny * __float_as_uint(bz.y)) - bias));
+                        // a + cos u + sin w; the texture unit takes the floor and the voxel's address
+                        const float2 tx = __ffma2_rn(s2, wx[a], __ffma2_rn(c2, ux[a], ax[a]));
+                        const float2 ty = __ffma2_rn(s2, wy[a], __ffma2_rn(c2, uy[a], ay[a]));
+                        const float2 tz = __ffma2_rn(s2, wz[a], __ffma2_rn(c2, uz[a], az[a]));
+                        acc[j] += tex3D<unsigned>(pd.Kt, tx.x, ty.x, tz.x);
+                        acc[j + 1] += tex3D<unsigned>(pd.Kt, tx.y, ty.y, tz.y);
                     }
                 }
             }
