@@ -94,7 +94,7 @@ struct BatchH {
 struct Plan {
     int ntask = 0, npairs = 0, slice = 0;
     std::vector<int> task_off;  // first task of each pair (plain form: pair order)
-    std::unique_ptr<DevBuf> tasks, pockets, cs_hp, cs_lp, cs_peel;
+    std::unique_ptr<DevBuf> tasks, pockets, cs_hp, cs_lp, cs_peel, coarse;
     std::unique_ptr<DevBuf> skipped;  // per pair: pose-repetitions left out at a fixed point
     SweepParams P{};
     FinalParams F{};
@@ -951,6 +951,18 @@ int get_plan(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const doc
     P.repetitions = k->repetitions;
     P.slice = pl->slice;
     P.threshold = k->threshold;
+    {
+        // Alg. 2's step choice per sweep descriptor, decided once on the host
+        std::vector<uint8_t> co(std::max(1, B.nside_total), 0);
+        for (int b = 0; b < B.n; ++b)
+            for (int si = 0; si < B.nside[b]; ++si) {
+                const int g = B.side_off[b] + si;
+                co[g] = (double)B.side_m[g] / (double)B.l[b] <= k->threshold ? 1 : 0;
+            }
+        int rc = upload(ctx, pl->coarse, co.data(), co.size());
+        if (rc) return rc;
+    }
+    P.coarse = pl->coarse->as<uint8_t>();
     P.bump_thr = k->bump_thr;
     P.seed = k->seed;
     P.cs_hp = pl->cs_hp->as<float2>();

@@ -103,6 +103,8 @@ struct SweepParams {
     int n_poses;
     int repetitions;
     double threshold;
+    const uint8_t* coarse;  // per sweep descriptor: 1 when its relative size m/l <= threshold (Alg. 2),
+                            // decided on the host; NULL: decided here (an FP64 division per sweep)
     double bump_thr;     // Å
     uint64_t seed;
     const float2* cs_hp;  // cos/sin of k * hp_step, k = 0..P_hp-1
@@ -579,7 +581,8 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                 for (int si = 0; si < L.nside; ++si) {
                     const SideDev sd = P.side[L.side_off + si];
                     const int sweep = rep * L.nside + si;
-                    const bool coarse = (double)sd.m / (double)L.l <= P.threshold;
+                    const bool coarse =
+                        P.coarse ? P.coarse[L.side_off + si] != 0 : (double)sd.m / (double)L.l <= P.threshold;
                     const bool peel = P.peel && !coarse;
                     // the sweep's index lists, staged in shared memory: M\{c}, then F\{b}, b, c
                     __syncwarp();
