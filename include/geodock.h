@@ -191,6 +191,27 @@ int dock_release_batch(dock_ctx* ctx, int batch_id);
 int dock_run(dock_ctx* ctx, int batch_id, const int32_t* pocket_ids, int npockets, const dock_knobs* k,
              dock_result* out, float* xyz_out, int out_on_device, void* stream);
 
+/* Dock a ligand database held in host memory: the same results as
+ * dock_upload_ligands + dock_run (out_on_device 0) + dock_release_batch on the
+ * whole database, computed chunk by chunk with the host preparation and the
+ * upload of the next chunk overlapping the device sweep of the current one
+ * (two pipeline stages; their device and pinned host buffers stay with the
+ * context and are reused by later calls).
+ *   b                      the database (same layout and checks as
+ *                          dock_upload_ligands; a bad ligand is reported by
+ *                          the chunk holding it)
+ *   pocket_ids, npockets   host array of pocket handles (>= 1)
+ *   k                      knobs
+ *   chunk                  ligands per chunk (>= 1; more than n means one)
+ *   out                    npockets*n results, pocket-major, host memory
+ *   xyz_out                NULL, or npockets*3*atom_off[n] floats (host)
+ *   stream                 cudaStream_t of the sweeps (NULL: legacy stream)
+ * Waits for every chunk. dock_last_stats then reports the work of the whole
+ * database and sweep_ms = -1 (not timed). Errors as dock_upload_ligands and
+ * dock_run; results already written for earlier chunks stay in out. */
+int dock_run_database(dock_ctx* ctx, const dock_ligand_batch* b, const int32_t* pocket_ids, int npockets,
+                      const dock_knobs* k, int chunk, dock_result* out, float* xyz_out, void* stream);
+
 /* Per-candidate trace of one run on one pocket, for parity checks against a
  * reference implementation. Every pointer is device memory (nullable except
  * chosen_k). Sweep index of (ligand b, pose p, sweep s):

@@ -91,6 +91,8 @@ def _load():
         "dock_release_batch": ([vp, ctypes.c_int], ctypes.c_int),
         "dock_run": ([vp, ctypes.c_int, P(ctypes.c_int32), ctypes.c_int, P(dock_knobs), vp, vp, ctypes.c_int, vp],
                      ctypes.c_int),
+        "dock_run_database": ([vp, P(dock_ligand_batch), P(ctypes.c_int32), ctypes.c_int, P(dock_knobs), ctypes.c_int,
+                               vp, vp, vp], ctypes.c_int),
         "dock_run_trace": ([vp, ctypes.c_int, ctypes.c_int, P(dock_knobs), P(dock_trace), vp, vp], ctypes.c_int),
         "dock_trace_pmax": ([P(dock_knobs)], ctypes.c_int),
         "dock_set_tile": ([vp, P(dock_tile)], ctypes.c_int),
@@ -204,7 +206,9 @@ class Docker:
         self._check(lib.dock_pocket_field(self._c, pid, _ptr(K, ctypes.c_uint16)), "dock_pocket_field")
         return K.reshape(nz, ny, nx)
 
-    def upload_ligands(self, batch, ids=None) -> int:
+    @staticmethod
+    def _batch_struct(batch, ids=None):
+        """dock_ligand_batch over the batch's arrays; returns (struct, arrays to keep alive during the call)."""
         b = dock_ligand_batch()
         b.n = batch.n
         arrs = [np.ascontiguousarray(batch.atom_off, np.int32), np.ascontiguousarray(batch.xyz, np.float32),
@@ -220,9 +224,33 @@ class Docker:
         if ids is not None:
             ids = np.ascontiguousarray(ids, np.int64)
             b.ids = _ptr(ids, ctypes.c_int64)
+            arrs.append(ids)
+        return b, arrs
+
+    def upload_ligands(self, batch, ids=None) -> int:
+        b, keep = self._batch_struct(batch, ids)
         bid = ctypes.c_int(-1)
         self._check(lib.dock_upload_ligands(self._c, ctypes.byref(b), ctypes.byref(bid)), "dock_upload_ligands")
+        del keep
         return bid.value
+
+    def run_database(self, batch, pocket_ids, kn, chunk: int = 1024, xyz: bool = True, ids=None, stream=None):
+        """dock_run_database: dock a host-memory ligand database chunk by chunk (host preparation of the next
+        chunk overlapping the device sweep). Returns (results structured array, xyz array or None)."""
+        pids = np.ascontiguousarray(pocket_ids, np.int32).reshape(-1)
+        k = knobs_struct(kn)
+        npk, n = len(pids), int(batch.n)
+        natoms = int(batch.atom_off[-1]) if n else 0
+        b, keep = self._batch_struct(batch, ids)
+        out = np.zeros(npk * n, RESULT_DTYPE)
+        xyz_out = np.zeros((npk, natoms, 3), np.float32) if xyz else None
+        rc = lib.dock_run_database(self._c, ctypes.byref(b), _ptr(pids, ctypes.c_int32), npk, ctypes.byref(k), int(chunk),
+                                   ctypes.c_void_p(out.ctypes.data),
+                                   ctypes.c_void_p(xyz_out.ctypes.data) if xyz else None,
+                                   _stream_ptr(stream) if stream is not None else None)
+        del keep
+        self._check(rc, "dock_run_database")
+        return out, xyz_out
 
     def release_batch(self, bid: int):
         self._check(lib.dock_release_batch(self._c, bid), "dock_release_batch")

@@ -119,6 +119,47 @@ struct WorkTally {
     bool pending = false;
 };
 
+// A ligand batch prepared on the host: the device arrays' contents and their
+// places in one allocation.
+struct BatchImage {
+    std::vector<LigDev> lig;
+    std::vector<RefLigDev> rlig;
+    std::vector<SideDev> sides;
+    std::vector<uint8_t> idx;
+    std::vector<RefTorDev> rtor;
+    std::vector<uint32_t> check;
+    const float* xyz = nullptr;
+    size_t o_lig = 0, o_side = 0, o_idx = 0, o_xyz = 0, o_rlig = 0, o_rtor = 0, o_chk = 0, total = 0;
+};
+
+// One stage of the database pipeline (dock_run_database): a chunk of ligands
+// on the device with its plan, and pinned host memory for its upload and its
+// results. Two of them alternate.
+struct DbSlot {
+    BatchH B;
+    BatchImage im;
+    std::unique_ptr<DevBuf> mem;
+    Plan plan;
+    std::vector<int32_t> aoff, boff, roff;  // the chunk's offsets, from 0
+    void* stage = nullptr;
+    void* hres = nullptr;
+    void* hxyz = nullptr;
+    void* hskip = nullptr;
+    size_t stage_bytes = 0, hres_bytes = 0, hxyz_bytes = 0, hskip_bytes = 0;
+    cudaEvent_t up = nullptr, done = nullptr;
+    int c0 = 0, c1 = 0;
+    bool pending = false;
+    DbSlot() = default;
+    DbSlot(const DbSlot&) = delete;
+    DbSlot& operator=(const DbSlot&) = delete;
+    ~DbSlot() {
+        for (void* p : {stage, hres, hxyz, hskip})
+            if (p) cudaFreeHost(p);
+        if (up) cudaEventDestroy(up);
+        if (done) cudaEventDestroy(done);
+    }
+};
+
 struct dock_ctx {
     int device = 0;
     int num_sms = 1;
@@ -137,11 +178,14 @@ struct dock_ctx {
     WorkTally tally;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the sweep kernel(s) of the last run
     bool timed = false;
+    DbSlot db[2];                     // database pipeline stages
+    cudaStream_t copy = nullptr;      // its uploads (non-blocking)
     ~dock_ctx() {
         plans.clear();
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
         if (stage) cudaFreeHost(stage);
+        if (copy) cudaStreamDestroy(copy);
     }
 };
 
@@ -646,19 +690,25 @@ int dock_pocket_field(dock_ctx* ctx, int pocket_id, uint16_t* K) {
     return DOCK_OK;
 }
 
-int dock_upload_ligands(dock_ctx* ctx, const dock_ligand_batch* b, int* batch_id) {
-    if (!ctx || !b || !batch_id) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_upload_ligands: NULL argument");
+}  // extern "C"
+
+namespace {
+
+// Validate a batch and prepare it on the host (Alg. 1's fragment lists per
+// rotatable bond, refinement torsions, bump-pair rows); fills B's host fields.
+int prep_batch(dock_ctx* ctx, const dock_ligand_batch* b, BatchH& B, BatchImage& im) {
     if (b->n < 0) return fail(ctx, DOCK_ERR_INVALID_ARG, "batch: n < 0");
     if (b->n > 0 && (!b->atom_off || !b->xyz || !b->bond_off || !b->rot_off))
         return fail(ctx, DOCK_ERR_INVALID_ARG, "batch: NULL array");
     if (b->n > 0 && (b->atom_off[0] != 0 || b->bond_off[0] != 0 || b->rot_off[0] != 0))
         return fail(ctx, DOCK_ERR_INVALID_ARG, "batch: offsets must start at 0");
-    CK(cudaSetDevice(ctx->device));
     const int n = b->n;
-    BatchH B;
+    B = BatchH();
     B.n = n;
-    std::vector<LigDev> lig(n);
-    std::vector<RefLigDev> rlig(n);
+    std::vector<LigDev>& lig = im.lig;
+    std::vector<RefLigDev>& rlig = im.rlig;
+    lig.assign(n, LigDev{});
+    rlig.assign(n, RefLigDev{});
     // the ligands are independent: ranges of them are prepared in parallel, then joined in order
     const int hw = std::max(1, (int)std::thread::hardware_concurrency());
     const int nt = std::max(1, std::min(hw, n / 64));
@@ -681,10 +731,14 @@ int dock_upload_ligands(dock_ctx* ctx, const dock_ligand_batch* b, int* batch_id
         ntor += o.rtor.size();
         nchk += o.check.size();
     }
-    std::vector<SideDev> sides;
-    std::vector<uint8_t> idx;
-    std::vector<RefTorDev> rtor;
-    std::vector<uint32_t> check;
+    std::vector<SideDev>& sides = im.sides;
+    std::vector<uint8_t>& idx = im.idx;
+    std::vector<RefTorDev>& rtor = im.rtor;
+    std::vector<uint32_t>& check = im.check;
+    sides.clear();
+    idx.clear();
+    rtor.clear();
+    check.clear();
     sides.reserve(nside);
     idx.reserve(nidx);
     rtor.reserve(ntor);
@@ -720,41 +774,72 @@ int dock_upload_ligands(dock_ctx* ctx, const dock_ligand_batch* b, int* batch_id
     }
     B.natoms = n > 0 ? b->atom_off[n] : 0;
     B.nside_total = (int)sides.size();
-    // one device allocation and one copy from a pinned staging buffer
+    // one device allocation, 256-byte aligned parts
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t o_lig = 0, o_side = al(o_lig + lig.size() * sizeof(LigDev));
-    const size_t o_idx = al(o_side + sides.size() * sizeof(SideDev));
-    const size_t o_xyz = al(o_idx + idx.size());
-    const size_t o_rlig = al(o_xyz + (size_t)B.natoms * 3 * sizeof(float));
-    const size_t o_rtor = al(o_rlig + rlig.size() * sizeof(RefLigDev));
-    const size_t o_chk = al(o_rtor + rtor.size() * sizeof(RefTorDev));
-    const size_t total = al(o_chk + check.size() * sizeof(uint32_t)) + 256;
-    if (ctx->stage_bytes < total) {
-        if (ctx->stage) cudaFreeHost(ctx->stage);
-        ctx->stage = nullptr;
-        ctx->stage_bytes = 0;
-        CK(cudaHostAlloc(&ctx->stage, total, cudaHostAllocDefault));
-        ctx->stage_bytes = total;
-    }
+    im.xyz = b->xyz;
+    im.o_lig = 0;
+    im.o_side = al(im.o_lig + lig.size() * sizeof(LigDev));
+    im.o_idx = al(im.o_side + sides.size() * sizeof(SideDev));
+    im.o_xyz = al(im.o_idx + idx.size());
+    im.o_rlig = al(im.o_xyz + (size_t)B.natoms * 3 * sizeof(float));
+    im.o_rtor = al(im.o_rlig + rlig.size() * sizeof(RefLigDev));
+    im.o_chk = al(im.o_rtor + rtor.size() * sizeof(RefTorDev));
+    im.total = al(im.o_chk + check.size() * sizeof(uint32_t)) + 256;
+    return DOCK_OK;
+}
+
+// Write a prepared batch into host memory h (im.total bytes) in its device layout.
+void stage_batch(const BatchImage& im, int natoms, uint8_t* h) {
+    std::memcpy(h + im.o_lig, im.lig.data(), im.lig.size() * sizeof(LigDev));
+    std::memcpy(h + im.o_side, im.sides.data(), im.sides.size() * sizeof(SideDev));
+    std::memcpy(h + im.o_idx, im.idx.data(), im.idx.size());
+    if (natoms) std::memcpy(h + im.o_xyz, im.xyz, (size_t)natoms * 3 * sizeof(float));
+    std::memcpy(h + im.o_rlig, im.rlig.data(), im.rlig.size() * sizeof(RefLigDev));
+    std::memcpy(h + im.o_rtor, im.rtor.data(), im.rtor.size() * sizeof(RefTorDev));
+    std::memcpy(h + im.o_chk, im.check.data(), im.check.size() * sizeof(uint32_t));
+}
+
+// Point B's device arrays into the allocation d holding the staged image.
+void bind_batch(BatchH& B, const BatchImage& im, uint8_t* d) {
+    B.d_lig = reinterpret_cast<LigDev*>(d + im.o_lig);
+    B.d_side = reinterpret_cast<SideDev*>(d + im.o_side);
+    B.d_idx = d + im.o_idx;
+    B.d_xyz0 = reinterpret_cast<float*>(d + im.o_xyz);
+    B.d_rlig = reinterpret_cast<RefLigDev*>(d + im.o_rlig);
+    B.d_rtor = reinterpret_cast<RefTorDev*>(d + im.o_rtor);
+    B.d_check = reinterpret_cast<uint32_t*>(d + im.o_chk);
+}
+
+// Pinned host memory that grows on demand.
+int ensure_pinned(dock_ctx* ctx, void** p, size_t* have, size_t want) {
+    if (*have >= want && *p) return DOCK_OK;
+    if (*p) cudaFreeHost(*p);
+    *p = nullptr;
+    *have = 0;
+    CK(cudaHostAlloc(p, want, cudaHostAllocDefault));
+    *have = want;
+    return DOCK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dock_upload_ligands(dock_ctx* ctx, const dock_ligand_batch* b, int* batch_id) {
+    if (!ctx || !b || !batch_id) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_upload_ligands: NULL argument");
+    CK(cudaSetDevice(ctx->device));
+    BatchH B;
+    BatchImage im;
+    int rc = prep_batch(ctx, b, B, im);
+    if (rc) return rc;
+    // one device allocation and one copy from a pinned staging buffer
+    if ((rc = ensure_pinned(ctx, &ctx->stage, &ctx->stage_bytes, im.total))) return rc;
     uint8_t* h = static_cast<uint8_t*>(ctx->stage);
-    std::memcpy(h + o_lig, lig.data(), lig.size() * sizeof(LigDev));
-    std::memcpy(h + o_side, sides.data(), sides.size() * sizeof(SideDev));
-    std::memcpy(h + o_idx, idx.data(), idx.size());
-    if (B.natoms) std::memcpy(h + o_xyz, b->xyz, (size_t)B.natoms * 3 * sizeof(float));
-    std::memcpy(h + o_rlig, rlig.data(), rlig.size() * sizeof(RefLigDev));
-    std::memcpy(h + o_rtor, rtor.data(), rtor.size() * sizeof(RefTorDev));
-    std::memcpy(h + o_chk, check.data(), check.size() * sizeof(uint32_t));
+    stage_batch(im, B.natoms, h);
     B.mem.reset(new DevBuf());
-    CK(B.mem->ensure(total));
-    CK(cudaMemcpy(B.mem->p, h, total, cudaMemcpyHostToDevice));
-    uint8_t* d = B.mem->as<uint8_t>();
-    B.d_lig = reinterpret_cast<LigDev*>(d + o_lig);
-    B.d_side = reinterpret_cast<SideDev*>(d + o_side);
-    B.d_idx = d + o_idx;
-    B.d_xyz0 = reinterpret_cast<float*>(d + o_xyz);
-    B.d_rlig = reinterpret_cast<RefLigDev*>(d + o_rlig);
-    B.d_rtor = reinterpret_cast<RefTorDev*>(d + o_rtor);
-    B.d_check = reinterpret_cast<uint32_t*>(d + o_chk);
+    CK(B.mem->ensure(im.total));
+    CK(cudaMemcpy(B.mem->p, h, im.total, cudaMemcpyHostToDevice));
+    bind_batch(B, im, B.mem->as<uint8_t>());
     B.live = true;
     ctx->batches.push_back(std::move(B));
     *batch_id = (int)ctx->batches.size() - 1;
@@ -847,12 +932,40 @@ dock_tile resolve_tile(dock_ctx* ctx, int batch_id, const dock_knobs* k) {
     return t;
 }
 
-int upload(dock_ctx* ctx, std::unique_ptr<DevBuf>& buf, const void* src, size_t bytes) {
-    buf.reset(new DevBuf());
+// Copy host data into buf (allocated, or grown, on demand). With a stream the
+// copy is enqueued there (a pageable source is staged before the call returns).
+int upload(dock_ctx* ctx, std::unique_ptr<DevBuf>& buf, const void* src, size_t bytes, cudaStream_t cs = nullptr) {
+    if (!buf) buf.reset(new DevBuf());
     CK(buf->ensure(bytes));
-    if (bytes) CK(cudaMemcpy(buf->p, src, bytes, cudaMemcpyHostToDevice));
+    if (bytes) {
+        if (cs) CK(cudaMemcpyAsync(buf->p, src, bytes, cudaMemcpyHostToDevice, cs));
+        else CK(cudaMemcpy(buf->p, src, bytes, cudaMemcpyHostToDevice));
+    }
     return DOCK_OK;
 }
+
+// The context's scratch (queue head, per-pose keys and coordinates, per-pair
+// results) sized for a run of np pockets x nlig ligands (natoms atoms) x N
+// poses. Growing it moves the buffers, so every cached plan (and its captured
+// graph) is dropped.
+int ensure_scratch(dock_ctx* ctx, int np, int nlig, int natoms, int N) {
+    const int64_t npairs = (int64_t)np * nlig;
+    const size_t need[5] = {sizeof(unsigned), (size_t)npairs * N * sizeof(unsigned long long),
+                            (size_t)np * natoms * N * 3 * sizeof(float), (size_t)npairs * sizeof(dock_result),
+                            (size_t)np * natoms * 3 * sizeof(float)};
+    DevBuf* bufs[5] = {&ctx->counter, &ctx->pose_key, &ctx->pose_xyz, &ctx->res, &ctx->xyz_res};
+    bool grow = false;
+    for (int i = 0; i < 5; ++i) grow = grow || !bufs[i]->p || bufs[i]->n < need[i];
+    if (grow) {
+        CK(cudaDeviceSynchronize());
+        ctx->plans.clear();
+        for (int i = 0; i < 5; ++i) CK(bufs[i]->ensure(need[i]));
+    }
+    return DOCK_OK;
+}
+
+int build_plan(dock_ctx* ctx, const BatchH& B, const int32_t* pids, int np, const dock_knobs* k, const dock_tile& t,
+               int plain, Plan* pl, cudaStream_t cs);
 
 // Build (or fetch) the plan of a run: pockets, angle tables, tasks, launch shape.
 int get_plan(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const dock_knobs* k, int plain, Plan** out) {
@@ -864,7 +977,20 @@ int get_plan(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const doc
         return DOCK_OK;
     }
     const BatchH& B = ctx->batches[batch_id];
+    int rc = ensure_scratch(ctx, np, B.n, B.natoms, k->n_poses);
+    if (rc) return rc;
     std::unique_ptr<Plan> pl(new Plan());
+    if ((rc = build_plan(ctx, B, pids, np, k, t, plain, pl.get(), nullptr))) return rc;
+    *out = pl.get();
+    ctx->plans[key] = std::move(pl);
+    return DOCK_OK;
+}
+
+// Fill a plan for batch B: pockets, angle tables, tasks, step choices, launch
+// shape. Its buffers are reused when big enough; with a stream cs the uploads
+// are enqueued there. The context's scratch must already fit the run.
+int build_plan(dock_ctx* ctx, const BatchH& B, const int32_t* pids, int np, const dock_knobs* k, const dock_tile& t,
+               int plain, Plan* pl, cudaStream_t cs) {
     pl->Q = t.lanes_per_pose;
     pl->kc = t.angles_per_chunk;
     pl->W = t.warps_per_cta;
@@ -875,7 +1001,7 @@ int get_plan(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const doc
     // pockets
     std::vector<PocketDev> pd(np);
     for (int i = 0; i < np; ++i) pd[i] = ctx->pockets[pids[i]].d;
-    int rc = upload(ctx, pl->pockets, pd.data(), pd.size() * sizeof(PocketDev));
+    int rc = upload(ctx, pl->pockets, pd.data(), pd.size() * sizeof(PocketDev), cs);
     if (rc) return rc;
     // angle tables (host FP64 cos/sin rounded to FP32)
     const int P_hp = n_angles(k->hp_step), P_lp = n_angles(k->lp_step);
@@ -891,9 +1017,9 @@ int get_plan(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const doc
     } else {
         a_peel.push_back(0.0);
     }
-    if ((rc = upload(ctx, pl->cs_hp, angle_table(a_hp).data(), P_hp * sizeof(float2)))) return rc;
-    if ((rc = upload(ctx, pl->cs_lp, angle_table(a_lp).data(), P_lp * sizeof(float2)))) return rc;
-    if ((rc = upload(ctx, pl->cs_peel, angle_table(a_peel).data(), a_peel.size() * sizeof(float2)))) return rc;
+    if ((rc = upload(ctx, pl->cs_hp, angle_table(a_hp).data(), P_hp * sizeof(float2), cs))) return rc;
+    if ((rc = upload(ctx, pl->cs_lp, angle_table(a_lp).data(), P_lp * sizeof(float2), cs))) return rc;
+    if ((rc = upload(ctx, pl->cs_peel, angle_table(a_peel).data(), a_peel.size() * sizeof(float2), cs))) return rc;
     // tasks: (pair, pose group); batched form in descending cost (longest first),
     // plain form in pair order
     std::vector<int2> tasks;
@@ -920,22 +1046,7 @@ int get_plan(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const doc
         tasks.swap(sorted);
     }
     pl->ntask = (int)tasks.size();
-    if ((rc = upload(ctx, pl->tasks, tasks.data(), tasks.size() * sizeof(int2)))) return rc;
-    // scratch, shared by every plan of the context: growing it moves the
-    // buffers, so every cached plan (and its captured graph) is dropped
-    {
-        const size_t need[5] = {sizeof(unsigned), (size_t)pl->npairs * N * sizeof(unsigned long long),
-                                (size_t)np * B.natoms * N * 3 * sizeof(float), (size_t)pl->npairs * sizeof(dock_result),
-                                (size_t)np * B.natoms * 3 * sizeof(float)};
-        DevBuf* bufs[5] = {&ctx->counter, &ctx->pose_key, &ctx->pose_xyz, &ctx->res, &ctx->xyz_res};
-        bool grow = false;
-        for (int i = 0; i < 5; ++i) grow = grow || !bufs[i]->p || bufs[i]->n < need[i];
-        if (grow) {
-            CK(cudaDeviceSynchronize());
-            ctx->plans.clear();
-            for (int i = 0; i < 5; ++i) CK(bufs[i]->ensure(need[i]));
-        }
-    }
+    if ((rc = upload(ctx, pl->tasks, tasks.data(), tasks.size() * sizeof(int2), cs))) return rc;
     SweepParams& P = pl->P;
     P.lig = B.d_lig;
     P.side = B.d_side;
@@ -959,8 +1070,7 @@ int get_plan(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const doc
                 const int g = B.side_off[b] + si;
                 co[g] = (double)B.side_m[g] / (double)B.l[b] <= k->threshold ? 1 : 0;
             }
-        int rc = upload(ctx, pl->coarse, co.data(), co.size());
-        if (rc) return rc;
+        if ((rc = upload(ctx, pl->coarse, co.data(), co.size(), cs))) return rc;
     }
     P.coarse = pl->coarse->as<uint8_t>();
     P.bump_thr = k->bump_thr;
@@ -978,7 +1088,7 @@ int get_plan(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const doc
     P.per_tile = per_tile;
     P.pose_key = ctx->pose_key.as<unsigned long long>();
     P.pose_xyz = ctx->pose_xyz.as<float>();
-    pl->skipped.reset(new DevBuf());
+    if (!pl->skipped) pl->skipped.reset(new DevBuf());
     CK(pl->skipped->ensure((size_t)std::max(1, pl->npairs) * sizeof(unsigned)));
     P.skipped = pl->skipped->as<unsigned>();
     P.trace_on = 0;
@@ -1002,8 +1112,6 @@ int get_plan(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const doc
     F.shift = k->score_mode == 1 ? 0.0f : 0.5f;
     F.score = ctx->res.as<float>();
     F.xyz_out = ctx->xyz_res.as<float>();
-    *out = pl.get();
-    ctx->plans[key] = std::move(pl);
     return DOCK_OK;
 }
 
@@ -1068,8 +1176,35 @@ int check_run_args(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, con
     return DOCK_OK;
 }
 
+// Work of one repetition of one pose of ligand b over its 2T sweeps (Alg. 2's
+// step choice per sweep): candidates, moving-atom placements, circle bounds
+// (every pair once per sweep) and candidate bump pairs.
+struct LigWork {
+    uint64_t cand = 0, upd = 0, bounds = 0, pairs = 0;
+};
+LigWork lig_work(const BatchH& B, int b, const dock_knobs* k) {
+    const int P_hp = n_angles(k->hp_step), P_lp = n_angles(k->lp_step);
+    LigWork w;
+    for (int s = 0; s < B.nside[b]; ++s) {
+        const int si = B.side_off[b] + s;
+        const bool coarse = (double)B.side_m[si] / (double)B.l[b] <= k->threshold;
+        int phases[2] = {coarse ? P_lp - 1 : P_hp - 1, 0};
+        if (k->enable_refinement && !coarse) {
+            const int x = peel_tile(k->hp_step);
+            phases[0] = 360 / x;
+            phases[1] = (int)std::lround(x / k->hp_step);
+        }
+        for (int nc : phases) {
+            w.cand += nc;
+            w.upd += (uint64_t)nc * B.side_nmov[si];
+            w.pairs += (uint64_t)nc * B.side_nmov[si] * B.side_nfixB[si];
+        }
+        w.bounds += (uint64_t)B.side_nmov[si] * B.side_nfixB[si];
+    }
+    return w;
+}
+
 void count_work(dock_ctx* ctx, const BatchH& B, int np, const dock_knobs* k, const Plan* pl, uint64_t launches) {
-    int P_hp = n_angles(k->hp_step), P_lp = n_angles(k->lp_step);
     uint64_t cand = 0, upd = 0, bounds = 0, pairs = 0;
     WorkTally& W = ctx->tally;
     W.cand.assign(B.n, 0);
@@ -1077,28 +1212,16 @@ void count_work(dock_ctx* ctx, const BatchH& B, int np, const dock_knobs* k, con
     W.bounds.assign(B.n, 0);
     W.pairs.assign(B.n, 0);
     for (int b = 0; b < B.n; ++b) {
-        const uint64_t c0 = cand, u0 = upd, b0 = bounds, p0 = pairs;
-        for (int s = 0; s < B.nside[b]; ++s) {
-            int si = B.side_off[b] + s;
-            bool coarse = (double)B.side_m[si] / (double)B.l[b] <= k->threshold;
-            std::vector<int> phases{coarse ? P_lp - 1 : P_hp - 1};
-            if (k->enable_refinement && !coarse) {
-                int x = peel_tile(k->hp_step);
-                phases = {360 / x, (int)std::lround(x / k->hp_step)};
-            }
-            for (int nc : phases) {
-                cand += nc;
-                upd += (uint64_t)nc * B.side_nmov[si];
-                pairs += (uint64_t)nc * B.side_nmov[si] * B.side_nfixB[si];
-            }
-            // the circle bound tests every pair once per sweep
-            bounds += (uint64_t)B.side_nmov[si] * B.side_nfixB[si];
-        }
         // one repetition of one pose of ligand b
-        W.cand[b] = cand - c0;
-        W.upd[b] = upd - u0;
-        W.bounds[b] = bounds - b0;
-        W.pairs[b] = pairs - p0;
+        const LigWork w = lig_work(B, b, k);
+        W.cand[b] = w.cand;
+        W.upd[b] = w.upd;
+        W.bounds[b] = w.bounds;
+        W.pairs[b] = w.pairs;
+        cand += w.cand;
+        upd += w.upd;
+        bounds += w.bounds;
+        pairs += w.pairs;
     }
     W.nlig = B.n;
     W.npairs = np * B.n;
@@ -1171,6 +1294,175 @@ int dock_run(dock_ctx* ctx, int batch_id, const int32_t* pocket_ids, int npocket
     if (xyz_out && xbytes) CK(cudaMemcpyAsync(xyz_out, ctx->xyz_res.p, xbytes, kind, s));
     if (!out_on_device) CK(cudaStreamSynchronize(s));
     count_work(ctx, B, npockets, k, pl, launches);
+    return DOCK_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Wait for a pipeline stage's chunk, scatter its results into the caller's
+// arrays (pair = pocket * n + ligand; coordinates pocket-major) and add its
+// work, less the repetitions left out at fixed points, to the totals.
+int finish_chunk(dock_ctx* ctx, DbSlot& S, const dock_ligand_batch* b, int np, const dock_knobs* k,
+                 dock_result* out, float* xyz_out, dock_stats& tot) {
+    CK(cudaEventSynchronize(S.done));
+    S.pending = false;
+    const int n = b->n, nc = S.c1 - S.c0;
+    const int natoms = b->atom_off[n];
+    const int a0 = b->atom_off[S.c0], na = b->atom_off[S.c1] - a0;
+    const dock_result* r = static_cast<const dock_result*>(S.hres);
+    for (int pk = 0; pk < np; ++pk) std::memcpy(out + (size_t)pk * n + S.c0, r + (size_t)pk * nc, nc * sizeof(dock_result));
+    if (xyz_out)
+        for (int pk = 0; pk < np; ++pk)
+            std::memcpy(xyz_out + ((size_t)pk * natoms + a0) * 3, static_cast<const float*>(S.hxyz) + (size_t)pk * na * 3,
+                        (size_t)na * 3 * sizeof(float));
+    const unsigned* sk = static_cast<const unsigned*>(S.hskip);
+    const uint64_t mult = (uint64_t)k->n_poses * k->repetitions;
+    for (int i = 0; i < nc; ++i) {
+        const LigWork w = lig_work(S.B, i, k);
+        for (int pk = 0; pk < np; ++pk) {
+            const uint64_t reps = mult - sk[(size_t)pk * nc + i];
+            tot.candidates += reps * w.cand;
+            tot.atom_updates += reps * w.upd;
+            tot.pair_bounds += reps * w.bounds;
+            tot.bump_pairs += reps * w.pairs;
+            tot.pose_reps_skipped += sk[(size_t)pk * nc + i];
+        }
+    }
+    return DOCK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dock_run_database(dock_ctx* ctx, const dock_ligand_batch* b, const int32_t* pocket_ids, int npockets,
+                      const dock_knobs* k, int chunk, dock_result* out, float* xyz_out, void* stream) {
+    if (!ctx) return DOCK_ERR_INVALID_ARG;
+    if (!b || !out) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_run_database: NULL argument");
+    if (chunk < 1) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_run_database: chunk < 1");
+    if (npockets < 1 || !pocket_ids) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_run_database: no pockets");
+    for (int i = 0; i < npockets; ++i)
+        if (pocket_ids[i] < 0 || pocket_ids[i] >= (int)ctx->pockets.size() || !ctx->pockets[pocket_ids[i]].live)
+            return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_run_database: bad pocket id %d", pocket_ids[i]);
+    int rc = check_knobs(ctx, k);
+    if (rc) return rc;
+    if (k->score_mode == 2)
+        for (int i = 0; i < npockets; ++i)
+            if (ctx->pockets[pocket_ids[i]].d.npts < 1)
+                return fail(ctx, DOCK_ERR_UNSUPPORTED, "exact score: pocket %d was given without probe points",
+                            pocket_ids[i]);
+    if (b->n < 0) return fail(ctx, DOCK_ERR_INVALID_ARG, "batch: n < 0");
+    const int n = b->n;
+    ctx->stats = dock_stats{};
+    ctx->tally.pending = false;
+    ctx->timed = false;
+    ctx->stats.sweep_ms = -1.0;
+    if (n == 0) return DOCK_OK;
+    if (!b->atom_off || !b->xyz || !b->bond_off || !b->rot_off)
+        return fail(ctx, DOCK_ERR_INVALID_ARG, "batch: NULL array");
+    if (b->atom_off[0] != 0 || b->bond_off[0] != 0 || b->rot_off[0] != 0)
+        return fail(ctx, DOCK_ERR_INVALID_ARG, "batch: offsets must start at 0");
+    for (int i = 0; i < n; ++i)
+        if (b->atom_off[i + 1] < b->atom_off[i] || b->bond_off[i + 1] < b->bond_off[i] || b->rot_off[i + 1] < b->rot_off[i])
+            return fail(ctx, DOCK_ERR_INVALID_ARG, "batch: offsets must not decrease (ligand %d)", i);
+    chunk = std::min(chunk, n);
+    if ((int64_t)npockets * chunk * k->n_poses > (int64_t)1 << 31)
+        return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_run_database: too many poses per chunk");
+    CK(cudaSetDevice(ctx->device));
+    const int nchunk = (n + chunk - 1) / chunk;
+    int max_atoms = 0;
+    for (int c = 0; c < nchunk; ++c)
+        max_atoms = std::max(max_atoms, b->atom_off[std::min(n, (c + 1) * chunk)] - b->atom_off[c * chunk]);
+    if ((rc = ensure_scratch(ctx, npockets, chunk, max_atoms, k->n_poses))) return rc;
+    if (!ctx->copy) CK(cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking));
+    for (DbSlot& S : ctx->db) {
+        // a call that failed part way may have left copies in flight into these buffers
+        if (S.pending) CK(cudaEventSynchronize(S.done));
+        S.pending = false;
+        if (!S.up) CK(cudaEventCreateWithFlags(&S.up, cudaEventDisableTiming));
+        if (!S.done) CK(cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming));
+    }
+    const cudaStream_t s = (cudaStream_t)stream;
+    dock_tile t = default_tile(k);
+    if (ctx->tile.lanes_per_pose) t.lanes_per_pose = ctx->tile.lanes_per_pose;
+    if (ctx->tile.angles_per_chunk) t.angles_per_chunk = ctx->tile.angles_per_chunk;
+    if (ctx->tile.warps_per_cta) t.warps_per_cta = ctx->tile.warps_per_cta;
+    if (k->score_mode == 2) t.angles_per_chunk = 12;
+    dock_stats tot{};
+    uint64_t launches = 0;
+    // Chunk i is prepared on the host while the device sweeps chunk i-1; its
+    // upload runs on the copy stream, its sweep, finalize and result copies on
+    // the caller's stream; the results of chunk i-1 are collected after chunk i
+    // is enqueued, so the device always has the next chunk waiting.
+    for (int c = 0; c < nchunk; ++c) {
+        DbSlot& S = ctx->db[c & 1];
+        if (S.pending && (rc = finish_chunk(ctx, S, b, npockets, k, out, xyz_out, tot))) return rc;
+        S.c0 = c * chunk;
+        S.c1 = std::min(n, S.c0 + chunk);
+        const int nc = S.c1 - S.c0;
+        const int a0 = b->atom_off[S.c0], e0 = b->bond_off[S.c0], r0 = b->rot_off[S.c0];
+        S.aoff.resize(nc + 1);
+        S.boff.resize(nc + 1);
+        S.roff.resize(nc + 1);
+        for (int i = 0; i <= nc; ++i) {
+            S.aoff[i] = b->atom_off[S.c0 + i] - a0;
+            S.boff[i] = b->bond_off[S.c0 + i] - e0;
+            S.roff[i] = b->rot_off[S.c0 + i] - r0;
+        }
+        dock_ligand_batch v = *b;
+        v.n = nc;
+        v.atom_off = S.aoff.data();
+        v.xyz = b->xyz + (size_t)3 * a0;
+        v.bond_off = S.boff.data();
+        v.bonds = b->bonds ? b->bonds + (size_t)2 * e0 : nullptr;
+        v.rot_off = S.roff.data();
+        v.rot = b->rot ? b->rot + r0 : nullptr;
+        v.id_base = b->id_base + S.c0;
+        v.ids = b->ids ? b->ids + S.c0 : nullptr;
+        if ((rc = prep_batch(ctx, &v, S.B, S.im))) {
+            // a bad ligand in chunk c: report it by its index in the database
+            ctx->err = "ligands " + std::to_string(S.c0) + ".." + std::to_string(S.c1 - 1) + ": " + ctx->err;
+            for (DbSlot& o : ctx->db)
+                if (o.pending) cudaEventSynchronize(o.done), o.pending = false;
+            return rc;
+        }
+        // headroom so that later chunks rarely grow the buffers (growing synchronizes)
+        const size_t total = S.im.total + S.im.total / 4;
+        if ((rc = ensure_pinned(ctx, &S.stage, &S.stage_bytes, total))) return rc;
+        stage_batch(S.im, S.B.natoms, static_cast<uint8_t*>(S.stage));
+        if (!S.mem) S.mem.reset(new DevBuf());
+        if (S.mem->n < S.im.total) CK(S.mem->ensure(total));
+        CK(cudaMemcpyAsync(S.mem->p, S.stage, S.im.total, cudaMemcpyHostToDevice, ctx->copy));
+        bind_batch(S.B, S.im, S.mem->as<uint8_t>());
+        S.B.live = true;
+        if ((rc = build_plan(ctx, S.B, pocket_ids, npockets, k, t, 0, &S.plan, ctx->copy))) return rc;
+        CK(cudaEventRecord(S.up, ctx->copy));
+        CK(cudaStreamWaitEvent(s, S.up, 0));
+        if ((rc = enqueue_batched(ctx, &S.plan, k, s))) return rc;
+        launches += (S.plan.ntask > 0 ? 1 : 0) + (S.plan.npairs > 0 ? 1 : 0);
+        const size_t rbytes = (size_t)npockets * nc * sizeof(dock_result);
+        const size_t xbytes = (size_t)npockets * S.B.natoms * 3 * sizeof(float);
+        const size_t kbytes = (size_t)npockets * nc * sizeof(unsigned);
+        if ((rc = ensure_pinned(ctx, &S.hres, &S.hres_bytes, rbytes + rbytes / 4))) return rc;
+        if ((rc = ensure_pinned(ctx, &S.hskip, &S.hskip_bytes, kbytes + kbytes / 4))) return rc;
+        CK(cudaMemcpyAsync(S.hres, ctx->res.p, rbytes, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(S.hskip, S.plan.skipped->p, kbytes, cudaMemcpyDeviceToHost, s));
+        if (xyz_out && xbytes) {
+            if ((rc = ensure_pinned(ctx, &S.hxyz, &S.hxyz_bytes, xbytes + xbytes / 4))) return rc;
+            CK(cudaMemcpyAsync(S.hxyz, ctx->xyz_res.p, xbytes, cudaMemcpyDeviceToHost, s));
+        }
+        CK(cudaEventRecord(S.done, s));
+        S.pending = true;
+        DbSlot& prev = ctx->db[(c + 1) & 1];
+        if (prev.pending && (rc = finish_chunk(ctx, prev, b, npockets, k, out, xyz_out, tot))) return rc;
+    }
+    for (DbSlot& S : ctx->db)
+        if (S.pending && (rc = finish_chunk(ctx, S, b, npockets, k, out, xyz_out, tot))) return rc;
+    tot.kernel_launches = launches;
+    tot.sweep_ms = -1.0;
+    ctx->stats = tot;
     return DOCK_OK;
 }
 
