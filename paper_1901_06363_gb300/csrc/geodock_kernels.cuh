@@ -617,13 +617,23 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                         kax.y *= inv;
                         kax.z *= inv;
                     }
-                    // fixed atoms' part of S: F plus the axis atom c
+                    // fixed atoms' part of S: F plus the axis atom c. With nearest-voxel values and
+                    // clipping, S_inc is the exact integer sum over the pose (inside the box), so when M
+                    // is the smaller side its complement in S_inc is the same value, from fewer lookups.
                     float S_fix = 0.f;
-                    for (int i = q; i < sd.nfixS; i += Q) {
-                        bool in;
-                        S_fix += term<MODE, CLIP>(pd, K, ld3(xs, fix[i], G, ps), &in);
+                    if (MODE == 0 && CLIP && nmov < sd.nfixS) {
+                        for (int i = q; i < nmov; i += Q) {
+                            bool in;
+                            S_fix += term<MODE, CLIP>(pd, K, ld3(xs, mov[i], G, ps), &in);
+                        }
+                        S_fix = S_inc - group_sum(S_fix, Q);
+                    } else {
+                        for (int i = q; i < sd.nfixS; i += Q) {
+                            bool in;
+                            S_fix += term<MODE, CLIP>(pd, K, ld3(xs, fix[i], G, ps), &in);
+                        }
+                        S_fix = group_sum(S_fix, Q);
                     }
-                    S_fix = group_sum(S_fix, Q);
 
                     unsigned long long best = make_key(S_inc, 0);
                     const float2* cs = coarse ? P.cs_lp : P.cs_hp;
