@@ -34,7 +34,7 @@ WORKLOAD = "batched: 1024 ligands (16-64 atoms, 2-12 rotatable bonds) x 1 pocket
 # DRAM bytes (read + write) of one sweep launch on this workload, from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid for the kernel source
 # with this sha256 prefix only; reported as null for any other source.
-NCU_TRAFFIC = {"kernel_sha256": "8917de67405d4f3a", "bytes": 2818560 + 11520}
+NCU_TRAFFIC = {"kernel_sha256": "a598e4fcb4fd7478", "bytes": 2522624 + 2560}
 
 
 def _traffic():
