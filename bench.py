@@ -343,6 +343,7 @@ def run_ours(args):
         "clocks": clocks,
         "gpu_launches": int(st["kernel_launches"]) * args.steps,
         "pose_reps_skipped_per_step": int(st["pose_reps_skipped"]),
+        "lookups_skipped_per_step": int(st["lookups_skipped"]),
     }
     print(json.dumps(line), flush=True)
     if dist:

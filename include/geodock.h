@@ -268,10 +268,11 @@ int dock_autotune(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs* 
 /* Work and timing of the last dock_run, counted from the topology and knobs:
  *   candidates       candidate angles evaluated, over all (pocket, ligand,
  *                    pose, sweep), excluding the incumbents
- *   atom_updates     (candidate, moving atom) pairs: each is one rotation and
- *                    one field lookup
- *   pair_bounds      (sweep, angle chunk, moving atom, partner atom) circle
- *                    bound tests of the bump check
+ *   atom_updates     (candidate, moving atom) pairs placed and looked up in
+ *                    the field: each is one rotation and one field lookup;
+ *                    excludes lookups_skipped
+ *   pair_bounds      (sweep, moving atom, partner atom) circle bound tests of
+ *                    the bump check
  *   bump_pairs       (candidate, atom pair) distance tests a bump check
  *                    without the circle bound would make
  *   kernel_launches  CUDA kernels launched by the call
@@ -282,7 +283,11 @@ int dock_autotune(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs* 
  *                    that commits no angle for a pose leaves it where it
  *                    was, so each further repetition would repeat it
  *                    exactly; a pose that starts outside the box (clip_box)
- *                    computes none; the counts above exclude that work */
+ *                    computes none; the counts above exclude that work
+ *   lookups_skipped  (candidate, moving atom) lookups not made because the
+ *                    bump check had already rejected every candidate of
+ *                    their block of angles for every pose computed in the
+ *                    warp (nearest-voxel score) */
 typedef struct {
     uint64_t candidates;
     uint64_t atom_updates;
@@ -291,6 +296,7 @@ typedef struct {
     uint64_t kernel_launches;
     double sweep_ms;
     uint64_t pose_reps_skipped;
+    uint64_t lookups_skipped;
 } dock_stats;
 
 int dock_last_stats(const dock_ctx* ctx, dock_stats* s);

@@ -66,7 +66,7 @@ class dock_tile(ctypes.Structure):
 class dock_stats(ctypes.Structure):
     _fields_ = [("candidates", ctypes.c_uint64), ("atom_updates", ctypes.c_uint64), ("pair_bounds", ctypes.c_uint64),
                 ("bump_pairs", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64), ("sweep_ms", ctypes.c_double),
-                ("pose_reps_skipped", ctypes.c_uint64)]
+                ("pose_reps_skipped", ctypes.c_uint64), ("lookups_skipped", ctypes.c_uint64)]
 
 
 class dock_refine_trace_buf(ctypes.Structure):

@@ -96,6 +96,7 @@ struct Plan {
     std::vector<int> task_off;  // first task of each pair (plain form: pair order)
     std::unique_ptr<DevBuf> tasks, pockets, cs_hp, cs_lp, cs_peel, coarse;
     std::unique_ptr<DevBuf> skipped;  // per pair: pose-repetitions left out at a fixed point
+    std::unique_ptr<DevBuf> looked;   // lookups left out by the gate (one u64)
     SweepParams P{};
     FinalParams F{};
     int kc = 12, Q = 1, W = 4, grid = 1, block = 128;
@@ -116,6 +117,7 @@ struct WorkTally {
     std::vector<uint64_t> cand, upd, bounds, pairs;
     int nlig = 0, npairs = 0;
     DevBuf* skipped = nullptr;
+    DevBuf* looked = nullptr;
     bool pending = false;
 };
 
@@ -145,7 +147,8 @@ struct DbSlot {
     void* hres = nullptr;
     void* hxyz = nullptr;
     void* hskip = nullptr;
-    size_t stage_bytes = 0, hres_bytes = 0, hxyz_bytes = 0, hskip_bytes = 0;
+    void* hlook = nullptr;
+    size_t stage_bytes = 0, hres_bytes = 0, hxyz_bytes = 0, hskip_bytes = 0, hlook_bytes = 0;
     cudaEvent_t up = nullptr, done = nullptr;
     int c0 = 0, c1 = 0;
     bool pending = false;
@@ -153,7 +156,7 @@ struct DbSlot {
     DbSlot(const DbSlot&) = delete;
     DbSlot& operator=(const DbSlot&) = delete;
     ~DbSlot() {
-        for (void* p : {stage, hres, hxyz, hskip})
+        for (void* p : {stage, hres, hxyz, hskip, hlook})
             if (p) cudaFreeHost(p);
         if (up) cudaEventDestroy(up);
         if (done) cudaEventDestroy(done);
@@ -904,9 +907,12 @@ int dock_last_stats(const dock_ctx* ctx_, dock_stats* s) {
             bd += sk[pair] * W.bounds[b];
             pr += sk[pair] * W.pairs[b];
         }
+        unsigned long long gated = 0;
+        if (W.looked) CK(cudaMemcpy(&gated, W.looked->p, sizeof gated, cudaMemcpyDeviceToHost));
         ctx->stats.pose_reps_skipped = reps;
+        ctx->stats.lookups_skipped = gated;
         ctx->stats.candidates -= c;
-        ctx->stats.atom_updates -= u;
+        ctx->stats.atom_updates -= u + gated;
         ctx->stats.pair_bounds -= bd;
         ctx->stats.bump_pairs -= pr;
         W.pending = false;
@@ -1091,6 +1097,9 @@ int build_plan(dock_ctx* ctx, const BatchH& B, const int32_t* pids, int np, cons
     if (!pl->skipped) pl->skipped.reset(new DevBuf());
     CK(pl->skipped->ensure((size_t)std::max(1, pl->npairs) * sizeof(unsigned)));
     P.skipped = pl->skipped->as<unsigned>();
+    if (!pl->looked) pl->looked.reset(new DevBuf());
+    CK(pl->looked->ensure(sizeof(unsigned long long)));
+    P.lookups_skipped = pl->looked->as<unsigned long long>();
     P.trace_on = 0;
     P.bw = bump_words(k);
     pl->smem = cta_smem(t, pl->slice, P.bw);
@@ -1119,6 +1128,7 @@ int build_plan(dock_ctx* ctx, const BatchH& B, const int32_t* pids, int np, cons
 int enqueue_batched(dock_ctx* ctx, Plan* pl, const dock_knobs* k, cudaStream_t s) {
     CK(cudaMemsetAsync(ctx->counter.p, 0, sizeof(unsigned), s));
     CK(cudaMemsetAsync(pl->skipped->p, 0, (size_t)std::max(1, pl->npairs) * sizeof(unsigned), s));
+    CK(cudaMemsetAsync(pl->looked->p, 0, sizeof(unsigned long long), s));
     // external event records become event nodes when this is captured into a graph; outside a
     // capture (the autotuner) they are plain records
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -1138,6 +1148,7 @@ int enqueue_batched(dock_ctx* ctx, Plan* pl, const dock_knobs* k, cudaStream_t s
 // sweep launch over that pair's pose groups, and finalize launch.
 int enqueue_plain(dock_ctx* ctx, Plan* pl, const dock_knobs* k, cudaStream_t s) {
     CK(cudaMemsetAsync(pl->skipped->p, 0, (size_t)std::max(1, pl->npairs) * sizeof(unsigned), s));
+    CK(cudaMemsetAsync(pl->looked->p, 0, sizeof(unsigned long long), s));
     CK(cudaEventRecord(ctx->ev0, s));
     for (int pair = 0; pair < pl->npairs; ++pair) {
         SweepParams P = pl->P;
@@ -1226,6 +1237,7 @@ void count_work(dock_ctx* ctx, const BatchH& B, int np, const dock_knobs* k, con
     W.nlig = B.n;
     W.npairs = np * B.n;
     W.skipped = pl ? pl->skipped.get() : nullptr;
+    W.looked = pl ? pl->looked.get() : nullptr;
     W.pending = W.skipped != nullptr;
     uint64_t mult = (uint64_t)np * k->n_poses * k->repetitions;
     ctx->stats.candidates = cand * mult;
@@ -1235,6 +1247,7 @@ void count_work(dock_ctx* ctx, const BatchH& B, int np, const dock_knobs* k, con
     ctx->stats.kernel_launches = launches;
     ctx->stats.sweep_ms = -1.0;
     ctx->stats.pose_reps_skipped = 0;
+    ctx->stats.lookups_skipped = 0;
     ctx->timed = true;
 }
 
@@ -1318,6 +1331,9 @@ int finish_chunk(dock_ctx* ctx, DbSlot& S, const dock_ligand_batch* b, int np, c
             std::memcpy(xyz_out + ((size_t)pk * natoms + a0) * 3, static_cast<const float*>(S.hxyz) + (size_t)pk * na * 3,
                         (size_t)na * 3 * sizeof(float));
     const unsigned* sk = static_cast<const unsigned*>(S.hskip);
+    const unsigned long long gated = *static_cast<const unsigned long long*>(S.hlook);
+    tot.lookups_skipped += gated;
+    tot.atom_updates -= gated;
     const uint64_t mult = (uint64_t)k->n_poses * k->repetitions;
     for (int i = 0; i < nc; ++i) {
         const LigWork w = lig_work(S.B, i, k);
@@ -1449,6 +1465,8 @@ int dock_run_database(dock_ctx* ctx, const dock_ligand_batch* b, const int32_t* 
         if ((rc = ensure_pinned(ctx, &S.hskip, &S.hskip_bytes, kbytes + kbytes / 4))) return rc;
         CK(cudaMemcpyAsync(S.hres, ctx->res.p, rbytes, cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(S.hskip, S.plan.skipped->p, kbytes, cudaMemcpyDeviceToHost, s));
+        if ((rc = ensure_pinned(ctx, &S.hlook, &S.hlook_bytes, sizeof(unsigned long long)))) return rc;
+        CK(cudaMemcpyAsync(S.hlook, S.plan.looked->p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         if (xyz_out && xbytes) {
             if ((rc = ensure_pinned(ctx, &S.hxyz, &S.hxyz_bytes, xbytes + xbytes / 4))) return rc;
             CK(cudaMemcpyAsync(S.hxyz, ctx->xyz_res.p, xbytes, cudaMemcpyDeviceToHost, s));
@@ -1481,6 +1499,8 @@ int dock_run_trace(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs*
     if ((rc = get_plan(ctx, batch_id, &pid, 1, k, 0, &pl))) return rc;
     SweepParams P = pl->P;
     P.trace_on = 1;
+    P.skipped = nullptr;  // the plan's work counters belong to dock_run
+    P.lookups_skipped = nullptr;
     P.tr.pmax = tr->pmax;
     P.tr.chosen_k = tr->chosen_k;
     P.tr.cand_S = tr->cand_S;

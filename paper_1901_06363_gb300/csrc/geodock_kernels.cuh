@@ -119,6 +119,9 @@ struct SweepParams {
     // per-pose results (scratch)
     unsigned long long* pose_key;  // (float bits of S) << 32 | pose; ~0 when skipped
     unsigned* skipped;             // per pair: pose-repetitions left out at a fixed point (nullable)
+    unsigned long long* lookups_skipped;  // (pose, candidate, moving atom) lookups left out because every
+                                          // working pose of the warp had the candidates' block infeasible
+                                          // (nullable)
     float* pose_xyz;               // grid units, ((pocket*natoms + atom_off)*N + p*l + i)*3
     int trace_on;
     TraceDev tr;
@@ -307,8 +310,8 @@ constexpr int BW = 7;
 // Besides its coordinate slice a warp keeps in shared memory only the bump
 // bits (bw words per lane), the phase's candidate angles (64 bw, plus a
 // chunk's worth of padding) and the sweep's atom-index lists (up to 258
-// bytes): the rest of the SM's shared memory serves as L1 cache for the field
-// lookups.
+// bytes; the area's last word holds the warp's count of gated lookups): the
+// rest of the SM's shared memory serves as L1 cache for the field lookups.
 constexpr int IDX_FLOATS = 68;
 // Entries of the phase's angle table past 64 bw: a chunk's worth for the
 // lookups, and the 12-candidate blocks of the bump tests.
@@ -372,6 +375,10 @@ __device__ __forceinline__ float outside2(const PocketDev& pd, float3 t) {
     return ex * ex + ey * ey + ez * ez;
 }
 
+// Candidates per block of the lookup gate: a block whose candidates are all
+// infeasible for every pose of the warp is not scored.
+__host__ __device__ constexpr int gate_block(int kc) { return kc % 6 == 0 ? 6 : 4; }
+
 // Field terms of moving atoms at the chunk's KC angles, added to acc. The
 // angles' (cos, sin) come from the warp's shared table (the same for every
 // lane). fast: every circle lies inside the box, so no bounds tests. With
@@ -399,7 +406,7 @@ __device__ __forceinline__ void score_atoms(const PocketDev& pd, const uint16_t*
             wz[a] = dup2(s[a].w.z);
         }
         // blocks of candidates that no pose of the warp needs (all infeasible) are skipped
-        constexpr int BLK = KC % 6 == 0 ? 6 : 4;
+        constexpr int BLK = gate_block(KC);
         static_assert(KC % 2 == 0 && BLK % 2 == 0, "candidates go in pairs");
 #pragma unroll
         for (int jb = 0; jb < KC; jb += BLK) {
@@ -488,6 +495,9 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
     float2* ptab = reinterpret_cast<float2*>(xs + P.slice + P.bw * 64);             // the phase's angles, paired
     uint8_t* sidx = reinterpret_cast<uint8_t*>(ptab + 64 * P.bw + ptab_pad(KC));    // the sweep's index lists
     unsigned long long* col = bump + lane;
+    // the last word of the index-list area (lists take at most 258 bytes): the warp's count of
+    // lookups left out by the gate in the current task
+    unsigned* wlook = reinterpret_cast<unsigned*>(sidx) + (IDX_FLOATS - 1);
     const float shift = MODE == 1 ? 0.0f : 0.5f;
 
     for (;;) {
@@ -574,6 +584,7 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
         // pose that starts outside the box computes none.
         bool conv = !live;
         unsigned nskip = 0;
+        if (lane == 0) *wlook = 0u;
         if (__any_sync(FULL, live)) {
             for (int rep = 0; rep < P.repetitions; ++rep) {
                 bool moved = false;  // did this pose commit any angle in this repetition
@@ -778,6 +789,7 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                                 const unsigned hi = __reduce_or_sync(FULL, (unsigned)(nd >> 32));
                                 need = ((uint64_t)hi << 32) | lo;
                             }
+
                             auto circle_inside = [&](const Split& sp) {
                                 const float rad = sqrtf(sp.u.x * sp.u.x + sp.u.y * sp.u.y + sp.u.z * sp.u.z) + 1e-3f;
                                 return sp.a.x - rad >= lo && sp.a.x + rad < hix && sp.a.y - rad >= lo &&
@@ -792,6 +804,22 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                                 Split one[1] = {turn(split(ld3(xs, mov[h0 ? i0 : 0], G, ps), gc, kax), pre)};
                                 const bool fast = __all_sync(FULL, circle_inside(one[0]) || !h0);
                                 if (h0) score_atoms<KC, MODE, CLIP, 1>(pd, K, bias, one, fast, cst, acc, pen, box, need);
+                            }
+                            // lookups left out by the gate: the valid candidates of blocks no pose needed,
+                            // for every moving atom of every working pose (counted as if every pass took
+                            // the fast path; the checked path scores all candidates, so this count is
+                            // never below the lookups actually left out)
+                            if (MODE == 0 && P.lookups_skipped) {
+                                const unsigned nw = __popc(__ballot_sync(FULL, work && q == 0));
+                                constexpr int BLK = gate_block(KC);
+                                const uint64_t vm = nvalid >= 64 ? ~0ull : ((1ull << nvalid) - 1ull);
+                                unsigned gone = 0;
+#pragma unroll
+                                for (int jb = 0; jb < KC; jb += BLK) {
+                                    const uint64_t m = (((1ull << BLK) - 1ull) << jb) & vm;
+                                    if (!(need & m)) gone += (unsigned)__popcll(m);
+                                }
+                                if (lane == 0 && gone && nw) *wlook += gone * (unsigned)nmov * nw;
                             }
                             // this chunk's bump bits
                             uint64_t bad;
@@ -883,6 +911,7 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
             for (int o = 16; o > 0; o >>= 1) nskip += __shfl_xor_sync(FULL, nskip, o);
             if (lane == 0 && nskip) atomicAdd(P.skipped + tk.x, nskip);
         }
+        if (P.lookups_skipped && lane == 0 && *wlook) atomicAdd(P.lookups_skipped, (unsigned long long)*wlook);
         // ---- per-pose result
         if (active && q == 0) {
             const int64_t pi = (int64_t)tk.x * P.n_poses + p;

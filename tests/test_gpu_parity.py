@@ -326,3 +326,48 @@ def test_fixed_point_repetitions_are_counted_out(dk, n_grid):
     if n_grid == 16:
         assert (g["pose_status"][:b.n * N] != 0).any()
     dk.release_batch(bid)
+
+
+def test_gated_lookups_are_counted_out(dk):
+    """Blocks of 6 candidates that the bump check rejected for every working pose of a warp are not scored; the
+    count of lookups left out equals a replay of that rule on the traced run's candidate statuses (ligands of at
+    most 32 atoms and 16 poses: one warp of 2 lanes per pose per ligand; 30 degrees: 11 candidates, blocks
+    [0, 6) and [6, 11))."""
+    import indep
+    pk = synth.pocket(8, 64, 0.5, C.ELLIPSOID)
+    l, t = synth.ligand_sizes(23, 24, 0, [16, 32, 1, 6])
+    b = synth.ligand_batch(23, l, t)
+    kn = C.knobs(n_poses=16, hp_step=30.0, lp_step=30.0, repetitions=3, bump_thr=2.6, seed=2)
+    pid = dk.init_pocket(pk)
+    bid = dk.upload_ligands(b)
+    res, _ = dk.run(bid, [pid], kn, b.n, _natoms(b))
+    st = dk.stats()
+    g = dk.run_trace(bid, pid, kn, b)
+    assert np.array_equal(res.view(np.int32), g["result"].view(np.int32))
+    N, R, nc = kn["n_poses"], kn["repetitions"], oracle.n_angles(30.0) - 1
+    pmax = len(g["cand_status"]) // len(g["chosen_k"])
+    status = g["cand_status"].reshape(-1, pmax)
+    expected, upd, side_off = 0, 0, 0
+    for i in range(b.n):
+        x, bonds, rot = indep.ligand(b, i)
+        sides = indep.sides(len(x), bonds, rot)
+        ns = len(sides)
+        nmov = [int(m.sum()) - 1 for m, _, _ in sides]
+        rows = lambda p, r: N * R * side_off + p * R * ns + r * ns  # noqa: E731
+        working = [g["pose_status"][i * N + p] == 0 for p in range(N)]
+        for r in range(R):
+            for si in range(ns):
+                cs = [status[rows(p, r) + si, 1:1 + nc] for p in range(N) if working[p]]
+                for a, e in ((0, 6), (6, nc)):
+                    if all((c[a:e] == 0).all() for c in cs):
+                        expected += len(cs) * (e - a) * nmov[si]
+                upd += len(cs) * nc * nmov[si]
+            # a pose that committed nothing in this repetition computes no further one
+            for p in range(N):
+                if working[p] and not any(g["chosen_k"][rows(p, r) + si] for si in range(ns)):
+                    working[p] = False
+        side_off += ns
+    assert expected > 0
+    assert st["lookups_skipped"] == expected
+    assert st["atom_updates"] == upd - expected
+    dk.release_batch(bid)
