@@ -34,7 +34,7 @@ WORKLOAD = "batched: 1024 ligands (16-64 atoms, 2-12 rotatable bonds) x 1 pocket
 # DRAM bytes (read + write) of one sweep launch on this workload, from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid for the kernel source
 # with this sha256 prefix only; reported as null for any other source.
-NCU_TRAFFIC = {"kernel_sha256": "a598e4fcb4fd7478", "bytes": 2522624 + 2560}
+NCU_TRAFFIC = {"kernel_sha256": "d43ae050bef64729", "bytes": 2522624 + 2816}
 
 
 def _traffic():
@@ -342,6 +342,7 @@ def run_ours(args):
         "e2e": e2e,
         "clocks": clocks,
         "gpu_launches": int(st["kernel_launches"]) * args.steps,
+        "work_per_step": {k: int(st[k]) for k in ("candidates", "atom_updates", "pair_bounds", "bump_pairs")},
         "pose_reps_skipped_per_step": int(st["pose_reps_skipped"]),
         "lookups_skipped_per_step": int(st["lookups_skipped"]),
     }
