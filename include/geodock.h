@@ -201,7 +201,8 @@ int dock_run(dock_ctx* ctx, int batch_id, const int32_t* pocket_ids, int npocket
  *                          dock_upload_ligands; a bad ligand is reported by
  *                          the chunk holding it)
  *   pocket_ids, npockets   host array of pocket handles (>= 1)
- *   k                      knobs
+ *   k                      knobs (plain_mode is ignored: the chunks always
+ *                          run the batched form)
  *   chunk                  ligands per chunk (>= 1; more than n means one)
  *   out                    npockets*n results, pocket-major, host memory
  *   xyz_out                NULL, or npockets*3*atom_off[n] floats (host)

@@ -7,10 +7,11 @@ per configuration and validated leave-one-pocket-out.
 
 Inputs are the seeded synthetic workloads: lognormal ligands (median 32 atoms, Poisson(6) rotatable
 bonds) on the 64^3 ellipsoid pocket for the sweep, and that pocket plus four pockets of 48^3-128^3 x four
-ligand groups (quartiles of atoms x rotatable bonds) for the model. Every run is a batched dock_run timed with CUDA
-events on its stream after one warm-up run of the same plan; the plain per-pair form is timed on a
-subset. Prints one JSON document. With --checkpoint, every finished shard (one configuration on the
-sweep set, its plain-form timing, one fit row) is kept in DIR and skipped when the run is restarted.
+ligand groups (quartiles of atoms x rotatable bonds) for the model. Every run is a batched dock_run
+timed with CUDA events on its stream after one warm-up run of the same plan (the median of three
+runs); the plain per-pair form is timed on a subset. Prints one JSON document. With --checkpoint,
+every finished shard (one configuration on the sweep set, its plain-form timing, one fit row) is kept
+in DIR and skipped when the run is restarted.
 """
 from __future__ import annotations
 
@@ -50,15 +51,19 @@ class Checkpoint:
         return res
 
 
-def _timed_run(dk, bid, pids, kn, n, natoms, out, xyz, stream, torch):
-    dk.run(bid, pids, kn, n, natoms, out=out, xyz_out=xyz, stream=stream)  # warm: builds and captures the plan
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
+def _timed_run(dk, bid, pids, kn, n, natoms, out, xyz, stream, torch, repeats=3):
+    """Median of `repeats` runs timed by CUDA events, after one warm-up run (plan build and capture)."""
     dk.run(bid, pids, kn, n, natoms, out=out, xyz_out=xyz, stream=stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / 1e3
+    times = []
+    for _ in range(repeats):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        dk.run(bid, pids, kn, n, natoms, out=out, xyz_out=xyz, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    return float(np.median(times))
 
 
 def run(ligands=100_000, fit_ligands=4_000, plain_ligands=128, seed=3, combos=None, log=None, checkpoint=None):

@@ -95,3 +95,18 @@ def test_database_errors(dk, setup):
     res, xyz, _ = _whole(dk, b, pids, kn)
     dres, dxyz = dk.run_database(b, pids, kn, chunk=64)
     assert np.array_equal(dres.view(np.int32), res.view(np.int32))
+
+
+@pytest.mark.parametrize("variant", ["peel", "trilinear", "noclip"])
+def test_database_knob_variants(dk, setup, variant):
+    """Tile peeling, the trilinear score and clipping off take the same path in chunks."""
+    pids, b, kn = setup
+    kn = dict(kn, **{"peel": dict(enable_refinement=1, hp_step=5.0, lp_step=30.0, n_poses=8),
+                     "trilinear": dict(score_mode=1),
+                     "noclip": dict(clip_box=0)}[variant])
+    sub = b.subset(np.arange(90))
+    res, xyz, st = _whole(dk, sub, pids, kn)
+    dres, dxyz = dk.run_database(sub, pids, kn, chunk=40)
+    assert np.array_equal(dres.view(np.int32), res.view(np.int32))
+    assert np.array_equal(dxyz, xyz)
+    assert dk.stats()["candidates"] == st["candidates"]
