@@ -235,7 +235,7 @@ def run_ours(args):
     # end to end through the C ABI with host buffers: the database call docks e2e_steps batches of the
     # workload (distinct ligand ids, so distinct poses) from host memory, one chunk per step: host
     # preparation and upload (H2D) of each chunk, its sweep, and its results and coordinates back (D2H)
-    e2e_steps = max(2, min(args.steps, 5))
+    e2e_steps = max(2, min(args.steps, 10))  # chunks of one database call: the pipeline fills once
     db = repeat_batch(batch, e2e_steps)
     dk.run_database(repeat_batch(batch, 2), [pid], kn, chunk=n)  # warm: both pipeline stages' buffers
     torch.cuda.synchronize()
