@@ -320,7 +320,9 @@ def run_ours(args):
     inst = 16.0 * st["atom_updates"] + 8.0 * st["pair_bounds"]
     sweep_avg = statistics.mean(sweep_ms)
     achieved = inst / (sweep_avg / 1e3) / 1e12
+    lookups_per_s = st["atom_updates"] / (sweep_avg / 1e3)
     clocks = clk.summary()
+    rates = dk.measure_peaks(pid, stream=stream)  # after the timed region
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -336,6 +338,11 @@ def run_ours(args):
                      "frac": achieved / peak_inst, "traffic": _traffic(), "traffic_unit": "bytes per launch (ncu)",
                      "kernel": "sweep_kernel", "sweep_ms": sweep_avg,
                      "peak_source": f"152 SMs x 128 lanes x sm_max_mhz {f_mhz:.0f} ({src} clocks)"},
+        "measured_rates": rates,
+        "gather_roofline": {"bound": "texture fetches", "achieved": lookups_per_s, "peak": rates["tex_local_per_s"],
+                            "unit": "fetches/s", "frac": lookups_per_s / rates["tex_local_per_s"],
+                            "note": "field lookups done by the sweep per second of sweep time, against the "
+                                    "measured point-sampled fetch rate within 16^3-voxel cubes"},
         "refine": refine,
         "exact_score": exact,
         "cpu_baseline": cpu_baseline(pk, batch, kn) if world == 1 else None,

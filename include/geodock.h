@@ -302,6 +302,32 @@ typedef struct {
 
 int dock_last_stats(const dock_ctx* ctx, dock_stats* s);
 
+/* Rates that bound the sweep, measured on the context's device (for the
+ * roofline of the measurement; not part of docking):
+ *   fma_per_s           FP32 fused multiply-adds per second (scalar fmaf,
+ *                       eight independent chains per thread, 2,048 threads
+ *                       per SM)
+ *   ffma2_per_s         the same with packed two-wide FP32 multiply-adds,
+ *                       counting both
+ *   tex_field_per_s     point-sampled fetches per second from the pocket's
+ *                       padded-field texture, coordinates spread over the
+ *                       whole field (L2-resident)
+ *   tex_local_per_s     the same within a 16^3-voxel cube per warp
+ *                       (L1-resident: the locality of one ligand's poses)
+ *   l2_sectors_per_s    random 32-byte sector loads per second from a 64 MiB
+ *                       buffer held in L2
+ * Each is timed with CUDA events on `stream` after a warm-up launch; the call
+ * allocates 65 MiB of device memory for its duration and waits. */
+typedef struct {
+    double fma_per_s;
+    double ffma2_per_s;
+    double tex_field_per_s;
+    double tex_local_per_s;
+    double l2_sectors_per_s;
+} dock_peaks;
+
+int dock_measure_peaks(dock_ctx* ctx, int pocket_id, dock_peaks* out, void* stream);
+
 /* dock_run for callers that cannot allocate device memory.
  *
  * The paper has no counterpart: this exists for the library's users. Some

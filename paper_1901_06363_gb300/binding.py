@@ -69,6 +69,11 @@ class dock_stats(ctypes.Structure):
                 ("pose_reps_skipped", ctypes.c_uint64), ("lookups_skipped", ctypes.c_uint64)]
 
 
+class dock_peaks(ctypes.Structure):
+    _fields_ = [("fma_per_s", ctypes.c_double), ("ffma2_per_s", ctypes.c_double), ("tex_field_per_s", ctypes.c_double),
+                ("tex_local_per_s", ctypes.c_double), ("l2_sectors_per_s", ctypes.c_double)]
+
+
 class dock_refine_trace_buf(ctypes.Structure):
     _fields_ = [("gstride", ctypes.c_int32), ("G", ctypes.c_void_p), ("D", ctypes.c_void_p), ("lam", ctypes.c_void_p),
                 ("S_new", ctypes.c_void_p), ("verdict", ctypes.c_void_p), ("accept", ctypes.c_void_p),
@@ -99,6 +104,7 @@ def _load():
         "dock_get_tile": ([vp, P(dock_tile)], ctypes.c_int),
         "dock_autotune": ([vp, ctypes.c_int, ctypes.c_int, P(dock_knobs), P(dock_tile), vp], ctypes.c_int),
         "dock_last_stats": ([vp, P(dock_stats)], ctypes.c_int),
+        "dock_measure_peaks": ([vp, ctypes.c_int, P(dock_peaks), vp], ctypes.c_int),
         "dock_run_static": ([vp, ctypes.c_int, ctypes.c_int, P(dock_knobs), vp, vp, vp], ctypes.c_int),
         "dock_batch_info": ([vp, ctypes.c_int, i32p, i32p, i32p, i32p], ctypes.c_int),
         "dock_score_trilinear": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp], ctypes.c_int),
@@ -335,6 +341,14 @@ class Docker:
         s = dock_stats()
         self._check(lib.dock_last_stats(self._c, ctypes.byref(s)), "dock_last_stats")
         return {name: getattr(s, name) for name, _ in dock_stats._fields_}
+
+    def measure_peaks(self, pid: int, stream=None):
+        """dock_measure_peaks: the device's measured FMA, texture-fetch and L2-sector rates (per second)."""
+        p = dock_peaks()
+        self._check(lib.dock_measure_peaks(self._c, pid, ctypes.byref(p),
+                                           _stream_ptr(stream) if stream is not None else None),
+                    "dock_measure_peaks")
+        return {name: getattr(p, name) for name, _ in dock_peaks._fields_}
 
     # ------------------------------------------- refinement and differentiable score
     def batch_info(self, bid: int):

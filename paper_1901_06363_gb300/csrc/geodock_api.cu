@@ -1353,6 +1353,24 @@ int finish_chunk(dock_ctx* ctx, DbSlot& S, const dock_ligand_batch* b, int np, c
 
 extern "C" {
 
+int dock_measure_peaks(dock_ctx* ctx, int pocket_id, dock_peaks* out, void* stream) {
+    if (!ctx) return DOCK_ERR_INVALID_ARG;
+    if (!out) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_measure_peaks: NULL out");
+    if (pocket_id < 0 || pocket_id >= (int)ctx->pockets.size() || !ctx->pockets[pocket_id].live)
+        return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_measure_peaks: bad pocket id %d", pocket_id);
+    CK(cudaSetDevice(ctx->device));
+    const PocketH& ph = ctx->pockets[pocket_id];
+    double r[5] = {0, 0, 0, 0, 0};
+    CK(gd::measure_peaks(ph.Kt->tex, ph.d.nx + 2 * PAD, ph.d.ny + 2 * PAD, ph.d.nz + 2 * PAD, ctx->num_sms,
+                         (cudaStream_t)stream, r));
+    out->fma_per_s = r[0];
+    out->ffma2_per_s = r[1];
+    out->tex_field_per_s = r[2];
+    out->tex_local_per_s = r[3];
+    out->l2_sectors_per_s = r[4];
+    return DOCK_OK;
+}
+
 int dock_run_database(dock_ctx* ctx, const dock_ligand_batch* b, const int32_t* pocket_ids, int npockets,
                       const dock_knobs* k, int chunk, dock_result* out, float* xyz_out, void* stream) {
     if (!ctx) return DOCK_ERR_INVALID_ARG;
