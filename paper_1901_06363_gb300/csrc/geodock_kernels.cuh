@@ -802,8 +802,9 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                                 const int i0 = q + Q * s;
                                 const bool h0 = i0 < nmov;
                                 Split one[1] = {turn(split(ld3(xs, mov[h0 ? i0 : 0], G, ps), gc, kax), pre)};
-                                const bool fast = __all_sync(FULL, circle_inside(one[0]) || !h0);
-                                if (h0) score_atoms<KC, MODE, CLIP, 1>(pd, K, bias, one, fast, cst, acc, pen, box, need);
+                                const bool fast = __all_sync(FULL, !h0 || !work || circle_inside(one[0]));
+                                // a pose not computed in this repetition makes no lookups (its lane idles)
+                                if (h0 && work) score_atoms<KC, MODE, CLIP, 1>(pd, K, bias, one, fast, cst, acc, pen, box, need);
                             }
                             // lookups left out by the gate: the valid candidates of blocks no pose needed,
                             // for every moving atom of every working pose (counted as if every pass took
