@@ -34,7 +34,7 @@ WORKLOAD = "batched: 1024 ligands (16-64 atoms, 2-12 rotatable bonds) x 1 pocket
 # DRAM bytes (read + write) of one sweep launch on this workload, from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid for the kernel source
 # with this sha256 prefix only; reported as null for any other source.
-NCU_TRAFFIC = {"kernel_sha256": "b522cf68b7dd935e", "bytes": 2558720 + 15616}
+NCU_TRAFFIC = {"kernel_sha256": "f94b1e889ba47020", "bytes": 2632192 + 768}
 
 
 def _traffic():

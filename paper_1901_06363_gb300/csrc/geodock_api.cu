@@ -64,7 +64,7 @@ struct FieldTex {
 struct PocketH {
     bool live = false;
     PocketDev d{};
-    std::unique_ptr<DevBuf> K, Kp;
+    std::unique_ptr<DevBuf> K;
     std::unique_ptr<FieldTex> Kt;
     std::unique_ptr<DevBuf> dev;  // device copy of d
     std::unique_ptr<DevBuf> pts;  // probe points for the exact score (float4, voxel + 0.5)
@@ -618,23 +618,23 @@ int dock_init_pocket(dock_ctx* ctx, const dock_pocket* p, int* pocket_id) {
         CK(cudaGetLastError());
         CK(cudaDeviceSynchronize());
     }
-    // padded 32-bit copy used by the sweep's unchecked lookups
+    // padded 32-bit copy for the sweep's unchecked lookups, held as a texture: point sampling at
+    // unnormalized coordinates returns the voxel at the floor of each coordinate, from a
+    // cache-friendly 3D layout; the linear copy is only the array's source
     {
         const int64_t np = (int64_t)(p->nx + 2 * PAD) * (p->ny + 2 * PAD) * (p->nz + 2 * PAD);
-        ph.Kp.reset(new DevBuf());
-        CK(ph.Kp->ensure(np * sizeof(uint32_t)));
-        pad_field_kernel<<<(unsigned)((np + 255) / 256), 256>>>(ph.Kp->as<uint32_t>(), ph.K->as<uint16_t>(), p->nx,
+        DevBuf lin;
+        CK(lin.ensure(np * sizeof(uint32_t)));
+        pad_field_kernel<<<(unsigned)((np + 255) / 256), 256>>>(lin.as<uint32_t>(), ph.K->as<uint16_t>(), p->nx,
                                                                 p->ny, p->nz);
         CK(cudaGetLastError());
         CK(cudaDeviceSynchronize());
-        // and as a texture: point sampling at unnormalized coordinates returns the voxel at the floor
-        // of each coordinate (the same voxel as the padded lookups), from a cache-friendly 3D layout
         const size_t ex = (size_t)(p->nx + 2 * PAD), ey = (size_t)(p->ny + 2 * PAD), ez = (size_t)(p->nz + 2 * PAD);
         ph.Kt.reset(new FieldTex());
         cudaChannelFormatDesc fd = cudaCreateChannelDesc<unsigned>();
         CK(cudaMalloc3DArray(&ph.Kt->arr, &fd, make_cudaExtent(ex, ey, ez)));
         cudaMemcpy3DParms cp = {};
-        cp.srcPtr = make_cudaPitchedPtr(ph.Kp->p, ex * sizeof(uint32_t), ex, ey);
+        cp.srcPtr = make_cudaPitchedPtr(lin.p, ex * sizeof(uint32_t), ex, ey);
         cp.dstArray = ph.Kt->arr;
         cp.extent = make_cudaExtent(ex, ey, ez);
         cp.kind = cudaMemcpyDeviceToDevice;
@@ -648,6 +648,7 @@ int dock_init_pocket(dock_ctx* ctx, const dock_pocket* p, int* pocket_id) {
         td.readMode = cudaReadModeElementType;
         td.normalizedCoords = 0;
         CK(cudaCreateTextureObject(&ph.Kt->tex, &rd, &td, nullptr));
+        CK(cudaDeviceSynchronize());  // before the linear copy is freed
     }
     // probe points for the exact score (Eq. 1's inner minimum without the grid)
     if (p->pts && p->npts > 0) {
@@ -665,7 +666,6 @@ int dock_init_pocket(dock_ctx* ctx, const dock_pocket* p, int* pocket_id) {
         ph.d.npts = p->npts;
     }
     ph.d.K = ph.K->as<uint16_t>();
-    ph.d.Kp = ph.Kp->as<uint32_t>();
     ph.d.Kt = ph.Kt->tex;
     ph.d.nx = p->nx;
     ph.d.ny = p->ny;

@@ -46,9 +46,9 @@ constexpr uint32_t OUTSIDE = 1u << 24;
 
 struct PocketDev {
     const uint16_t* K;   // floored field, x fastest
-    const uint32_t* Kp;  // the same values padded by PAD voxels per side, OUTSIDE beyond the grid
-    unsigned long long Kt;  // Kp as a 3D texture (point sampling, unnormalized coordinates): a fetch at
-                            // padded position t returns Kp at floor(t)
+    unsigned long long Kt;  // the same values padded by PAD voxels per side, OUTSIDE beyond the grid, as
+                            // a 3D texture (point sampling, unnormalized coordinates): a fetch at padded
+                            // position t returns the value of the voxel floor(t)
     const float4* pts;   // probe points (voxel index + 0.5, grid units) for the exact score; NULL if unknown
     int npts;
     int nx, ny, nz;
@@ -345,17 +345,6 @@ struct Acc<2> {
     using T = float;
 };
 
-// Value of the padded field at padded shifted position t (nearest mode), for
-// a position known to lie inside the padded box: floor by the
-// round-toward-zero trick, no bounds test. bias folds the 2^23 offsets.
-__device__ __forceinline__ uint32_t lookup_padded(const uint32_t* __restrict__ Kp, uint32_t pnx, uint32_t pny,
-                                                  uint32_t bias, float3 t) {
-    const uint32_t bx = __float_as_uint(__fadd_rz(t.x, 8388608.0f));
-    const uint32_t by = __float_as_uint(__fadd_rz(t.y, 8388608.0f));
-    const uint32_t bz = __float_as_uint(__fadd_rz(t.z, 8388608.0f));
-    return __ldg(Kp + (bx + pnx * (by + pny * bz) - bias));
-}
-
 // Nearest-voxel value with the bounds test (shifted grid position t): the value
 // of the voxel (clamped to the box when outside) and whether t is inside.
 __device__ __forceinline__ uint32_t lookup_checked(const PocketDev& pd, const uint16_t* __restrict__ K, float3 t,
@@ -385,7 +374,7 @@ __host__ __device__ constexpr int gate_block(int kc) { return kc % 6 == 0 ? 6 : 
 // CLIP an angle that puts an atom outside sets its bit in box; without CLIP
 // the lookup is clamped and the squared distance outside goes to pen.
 template <int KC, int MODE, bool CLIP, int NA>
-__device__ __forceinline__ void score_atoms(const PocketDev& pd, const uint16_t* __restrict__ K, uint32_t bias,
+__device__ __forceinline__ void score_atoms(const PocketDev& pd, const uint16_t* __restrict__ K,
                                             const Split (&s)[NA], bool fast, const float4* __restrict__ cst,
                                             typename Acc<MODE>::T (&acc)[KC], float (&pen)[KC], uint64_t& box,
                                             uint64_t need) {
@@ -514,8 +503,6 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
         const int pocket = tk.x / P.nlig, b = tk.x % P.nlig;
         const PocketDev& pd = P.pockets[pocket];
         const uint16_t* __restrict__ K = pd.K;
-        const uint32_t pnx = (uint32_t)(pd.nx + 2 * PAD), pny = (uint32_t)(pd.ny + 2 * PAD);
-        const uint32_t bias = 0x4B000000u * (1u + pnx + pnx * pny);
         const LigDev L = P.lig[b];
         const int p = (tk.y & 0xffff) * G + ps;
         const bool active = p < P.n_poses;
@@ -804,7 +791,7 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                                 Split one[1] = {turn(split(ld3(xs, mov[h0 ? i0 : 0], G, ps), gc, kax), pre)};
                                 const bool fast = __all_sync(FULL, !h0 || !work || circle_inside(one[0]));
                                 // a pose not computed in this repetition makes no lookups (its lane idles)
-                                if (h0 && work) score_atoms<KC, MODE, CLIP, 1>(pd, K, bias, one, fast, cst, acc, pen, box, need);
+                                if (h0 && work) score_atoms<KC, MODE, CLIP, 1>(pd, K, one, fast, cst, acc, pen, box, need);
                             }
                             // lookups left out by the gate: the valid candidates of blocks no pose needed,
                             // for every moving atom of every working pose (counted as if every pass took
