@@ -338,7 +338,7 @@ int dock_measure_peaks(dock_ctx* ctx, int pocket_id, dock_peaks* out, void* stre
  * its scratch on first use or when a batch grows; this call never does. Its
  * scratch (work-queue head, angle tables, pocket descriptor, task list,
  * per-pose keys and coordinates) lives in one file-scope device array of
- * about 50 MiB, which every GPU that loads the library holds until the
+ * about 51 MiB, which every GPU that loads the library holds until the
  * process exits.
  *
  * Same docking as dock_run on ONE pocket, same results; the batch and pocket

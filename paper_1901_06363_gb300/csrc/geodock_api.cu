@@ -1617,7 +1617,9 @@ constexpr size_t kOffTables = kOffPocket + align256(sizeof(PocketDev));
 constexpr size_t kOffTasks = kOffTables + align256(3 * kStaticAngles * sizeof(float2));
 constexpr size_t kOffKeys = kOffTasks + align256(kStaticPoseSlots * sizeof(int2));
 constexpr size_t kOffXyz = kOffKeys + align256(kStaticPoseSlots * sizeof(unsigned long long));
-constexpr size_t kStaticBytes = kOffXyz + align256(kStaticAtomPoses * 3 * sizeof(float));  // about 50 MiB
+constexpr int64_t kStaticSides = int64_t(1) << 20;  // sweep descriptors whose step choice is staged per call
+constexpr size_t kOffCoarse = kOffXyz + align256(kStaticAtomPoses * 3 * sizeof(float));
+constexpr size_t kStaticBytes = kOffCoarse + align256(kStaticSides);  // about 51 MiB
 
 }  // namespace
 
@@ -1740,6 +1742,17 @@ extern "C" int dock_run_static(dock_ctx* ctx, int batch_id, int pocket_id, const
     P.slice = slice;
     P.bw = bw;
     P.threshold = k->threshold;
+    if (B.nside_total <= kStaticSides) {
+        // Alg. 2's step choice per sweep descriptor, decided on the host (else in the kernel)
+        std::vector<uint8_t> co(std::max(1, B.nside_total), 0);
+        for (int b = 0; b < B.n; ++b)
+            for (int si = 0; si < B.nside[b]; ++si) {
+                const int g = B.side_off[b] + si;
+                co[g] = (double)B.side_m[g] / (double)B.l[b] <= k->threshold ? 1 : 0;
+            }
+        CK(cudaMemcpyAsync(base + kOffCoarse, co.data(), co.size(), cudaMemcpyHostToDevice, s));
+        P.coarse = base + kOffCoarse;
+    }
     P.bump_thr = k->bump_thr;
     P.seed = k->seed;
     const float2* tab = reinterpret_cast<const float2*>(base + kOffTables);

@@ -21,7 +21,9 @@ SCORE_REL = 1e-4  # per-score tolerance of the parity tests
 XYZ_ABS = 1e-3    # Å, final-pose tolerance of the parity tests
 
 
-def test_static_scratch_run_matches_dock_run():
+@pytest.mark.parametrize("threshold", [0.0, 0.3])
+def test_static_scratch_run_matches_dock_run(threshold):
+    """threshold 0.3 with a 30-degree low-precision step: the per-sweep step choice (Alg. 2) matters."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -31,7 +33,8 @@ def test_static_scratch_run_matches_dock_run():
     pk = synth.pocket(8, 64, 0.5, C.ELLIPSOID)
     l, t = synth.ligand_sizes(21, 24, 0, [16, 64, 2, 12])
     batch = synth.ligand_batch(21, l, t)
-    kn = C.knobs(n_poses=40, hp_step=15.0, lp_step=15.0, repetitions=2, seed=9)
+    kn = C.knobs(n_poses=40, hp_step=15.0, lp_step=30.0 if threshold else 15.0, threshold=threshold,
+                 repetitions=2, seed=9)
     n, natoms = batch.n, int(batch.atom_off[-1])
     pid = dk.init_pocket(pk)
     bid = dk.upload_ligands(batch)
