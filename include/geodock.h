@@ -166,8 +166,8 @@ int dock_init_pocket(dock_ctx* ctx, const dock_pocket* p, int* pocket_id);
 int dock_pocket_field(dock_ctx* ctx, int pocket_id, uint16_t* K);
 
 /* Upload a ligand batch: checks the topology, finds the two fragments of
- * every rotatable bond (Alg. 1: "grow the right and left fragment", the left
- * one holding the bond's lower atom index) and copies atoms and fragment
+ * every rotatable bond (Alg. 1: one on each side of the bond, the left one
+ * holding the bond's lower atom index) and copies atoms and fragment
  * tables to the GPU. *batch_id receives its handle. Synchronous.
  * Errors: DOCK_ERR_INVALID_ARG (sizes, indices), DOCK_ERR_TOPOLOGY. */
 int dock_upload_ligands(dock_ctx* ctx, const dock_ligand_batch* b, int* batch_id);

@@ -11,7 +11,7 @@
 //     points tabulated on a voxel grid (field K) or computed exactly;
 //   * rotamer and fragment detection (Sec. 2, Alg. 1);
 //   * fragment rotation about the rotamer bond (Alg. 1);
-//   * intra-ligand bump check (Alg. 1, "the ligand shape is feasible");
+//   * intra-ligand bump check (Alg. 1's feasibility test of the shape);
 //   * greedy left-then-right sweep per rotamer with strict improvement,
 //     repeated `repetitions` times, with the coarse step for fragments whose
 //     relative size is at most `threshold` (Alg. 2, Sec. 3.3);

@@ -1,6 +1,6 @@
 // Host side of the C ABI declared in include/geodock.h: context and device
-// memory, topology checks and fragment tables (Alg. 1 "get the list of
-// rotamers", "grow the right and left fragment"), run planning (work order,
+// memory, topology checks and fragment tables (Alg. 1: the rotatable bonds
+// and the two fragments on either side of each), run planning (work order,
 // angle tables), the persistent batched launch in a CUDA graph, the plain
 // one-launch-per-pair form, and the trace run.
 #include <cuda_runtime.h>

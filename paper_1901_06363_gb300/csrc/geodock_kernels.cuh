@@ -21,7 +21,7 @@
 // argmax is an exact integer comparison. Trilinear mode interpolates K; the
 // exact mode takes Eq. 1's inner minimum over the pocket points directly.
 //
-// Bump check (Alg. 1 "the ligand shape is feasible"): pairs (i in M\{c},
+// Bump check (Alg. 1's feasibility test of the shape): pairs (i in M\{c},
 // j in F\{b}). Atom i moves on a circle of radius r about the axis at axial
 // position h; a fixed atom y at radius rho and axial position t comes no
 // closer than sqrt((rho - r)^2 + (t - h)^2), so a pair whose closest approach
