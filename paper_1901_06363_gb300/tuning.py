@@ -13,8 +13,8 @@ per configuration:
     t = nu * (alpha(k) . x + beta(k)).
 
 Eq. 5 measures the accuracy loss of a configuration as the overlap
-degradation (1 - o_approx / o_original) * 100, each o being the mean overlap
-score of the top 1 % of the ligands.
+degradation (1 - o_approx / o_original) * 100, where each o averages the
+overlap scores of the best-scoring 1 % of the ligands.
 
 Knob selection (the paper delegates it to its autotuner): among the
 configurations whose predicted time fits the budget, take the one with the
