@@ -38,12 +38,13 @@ WORKLOAD = "batched: 1024 ligands (16-64 atoms, 2-12 rotatable bonds) x 1 pocket
 NCU_TRAFFIC = {"kernel_code_sha256": "ef309bda285fbcc3", "bytes": 2632192 + 768}
 
 
-def kernel_code_sha():
-    """sha256 prefix of the sweep kernel's source without comments and blank lines."""
+def kernel_code_sha(src=None):
+    """sha256 prefix of the sweep kernel's source (or of src) without comments and blank lines."""
     import hashlib
     import re
-    with open(os.path.join(ROOT, "paper_1901_06363_gb300", "csrc", "geodock_kernels.cuh")) as f:
-        src = f.read()
+    if src is None:
+        with open(os.path.join(ROOT, "paper_1901_06363_gb300", "csrc", "geodock_kernels.cuh")) as f:
+            src = f.read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     src = "\n".join(ln.split("//")[0].rstrip() for ln in src.splitlines())
     src = "\n".join(ln for ln in src.splitlines() if ln.strip())
