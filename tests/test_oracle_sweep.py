@@ -207,6 +207,34 @@ def test_repetitions_continue_from_their_own_output():
         assert np.all(np.diff(inc) <= 0)
 
 
+@pytest.mark.parametrize("seed", [61, 62, 63])
+def test_a_repetition_without_a_move_is_a_fixed_point(seed):
+    """A repetition that commits no angle leaves the pose where it started, so every later repetition repeats
+    it: the pose after R repetitions equals the pose after the first still one (what lets the GPU stop a pose
+    there). Checked against runs with more repetitions, pose by pose."""
+    pk, b, kn = _small_problem(l=18, t=3, seed=seed, step=20.0)
+    kn = dict(kn, n_poses=6)
+    opk = oracle.OraclePocket(pk)
+    R = 6
+    runs = {r: oracle.dock(opk, b, dict(kn, repetitions=r), trace=True, xyz_out=True) for r in range(1, R + 1)}
+    full = runs[R]
+    ns = full["nsweep"][0] // R
+    still = 0
+    for p in range(kn["n_poses"]):
+        ck = full["chosen_k"][p * R * ns:(p + 1) * R * ns].reshape(R, ns)
+        quiet = np.flatnonzero((ck == 0).all(axis=1))
+        if not len(quiet):
+            continue
+        still += 1
+        r0 = int(quiet[0]) + 1  # repetitions up to and including the first still one
+        assert (ck[r0:] == 0).all()  # nothing moves afterwards
+        for r in range(r0, R + 1):
+            assert runs[r]["pose_S"][p] == full["pose_S"][p]
+            xa = runs[r]["pose_xyz"].reshape(kn["n_poses"], -1, 3)[p]
+            assert np.array_equal(xa, full["pose_xyz"].reshape(kn["n_poses"], -1, 3)[p])
+    assert still > 0
+
+
 def test_threshold_selects_the_coarse_step():
     pk, b, kn = _small_problem(seed=51)
     opk = oracle.OraclePocket(pk)
