@@ -51,7 +51,7 @@ def test_database_matches_one_run(dk, setup, chunk):
     dst = dk.stats()
     assert np.array_equal(dres.view(np.int32), res.view(np.int32))
     assert np.array_equal(dxyz, xyz)
-    for key in ("candidates", "atom_updates", "pair_bounds", "bump_pairs", "pose_reps_skipped"):
+    for key in ("candidates", "atom_updates", "pair_bounds", "bump_pairs", "pose_reps_skipped", "lookups_skipped"):
         assert dst[key] == st[key], key
     assert dst["sweep_ms"] == -1.0
 
