@@ -228,7 +228,9 @@ class Docker:
         b.rot = _ptr(arrs[5], ctypes.c_int32)
         b.id_base = int(batch.id_base)
         if ids is not None:
-            ids = np.ascontiguousarray(ids, np.int64)
+            ids = np.ascontiguousarray(ids, np.int64).reshape(-1)
+            if len(ids) != batch.n:
+                raise ValueError(f"ids: {len(ids)} values for {batch.n} ligands")
             b.ids = _ptr(ids, ctypes.c_int64)
             arrs.append(ids)
         return b, arrs

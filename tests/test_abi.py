@@ -55,3 +55,21 @@ def test_refinement_calls_fail_cleanly_without_context(lib):
     assert g.lib.dock_dof_grad(None, 0, None, None, 6, None, None, None) == g.DOCK_ERR_INVALID_ARG
     assert g.lib.dock_refine(None, 0, None, 0, None, None, None, None, 0, None) == g.DOCK_ERR_INVALID_ARG
     assert g.lib.dock_refine_trace(None, 0, 0, None, None, None, None, None) == g.DOCK_ERR_INVALID_ARG
+
+
+def test_database_and_rate_calls_fail_cleanly_without_context(lib):
+    import paper_1901_06363_gb300 as g
+    assert g.lib.dock_run_database(None, None, None, 0, None, 1, None, None, None) == g.DOCK_ERR_INVALID_ARG
+    assert g.lib.dock_measure_peaks(None, 0, None, None) == g.DOCK_ERR_INVALID_ARG
+
+
+def test_batch_ids_must_match_the_ligand_count(lib):
+    import numpy as np
+    import synth
+    from paper_1901_06363_gb300 import Docker
+    l, t = synth.ligand_sizes(3, 4, 0, [12, 20, 1, 3])
+    b = synth.ligand_batch(3, l, t)
+    s, keep = Docker._batch_struct(b, ids=np.arange(4))
+    assert s.n == 4 and len(keep) == 7
+    with pytest.raises(ValueError):
+        Docker._batch_struct(b, ids=np.arange(3))
