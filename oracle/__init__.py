@@ -101,6 +101,9 @@ def _load():
             lib.oracle_score.argtypes = [P(Grid), ctypes.c_int, ctypes.c_int, P(ctypes.c_double), ctypes.c_int,
                                          P(ctypes.c_double), P(ctypes.c_int)]
             lib.oracle_score.restype = ctypes.c_int
+            lib.oracle_term.argtypes = [P(Grid), ctypes.c_int, ctypes.c_int, P(ctypes.c_double), ctypes.c_double,
+                                        P(ctypes.c_double), P(ctypes.c_int)]
+            lib.oracle_term.restype = ctypes.c_int
             lib.oracle_rotate.argtypes = [P(ctypes.c_double), ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double),
                                           ctypes.c_double, P(ctypes.c_double)]
             lib.oracle_rotate.restype = None
@@ -178,6 +181,21 @@ def score(opk: OraclePocket, xyz, mode=0, clip=1):
     _load().oracle_score(ctypes.byref(g), mode, clip, _ptr(x, ctypes.c_double), len(x), ctypes.byref(S),
                          ctypes.byref(inside))
     return S.value, bool(inside.value)
+
+
+def term(opk: OraclePocket, x, mode=0, clip=1, delta=0.0):
+    """One atom's term of Eq. 1 (grid units) with its parity band.
+
+    Returns (D, lo, hi, flags): lo and hi bound the term over the voxel-boundary alternatives of the
+    nearest-voxel lookup within delta grid units; flags bit0 inside the box, bit1 box band (an
+    alternative on the other side of the box edge), bit2 lo < hi."""
+    x = np.ascontiguousarray(x, np.float64).reshape(3)
+    out = np.zeros(3, np.float64)
+    flags = ctypes.c_int(0)
+    g = opk.cstruct()
+    _load().oracle_term(ctypes.byref(g), int(mode), int(clip), _ptr(x, ctypes.c_double), float(delta),
+                        _ptr(out, ctypes.c_double), ctypes.byref(flags))
+    return float(out[0]), float(out[1]), float(out[2]), int(flags.value)
 
 
 def rotate(xyz, c, b, theta):

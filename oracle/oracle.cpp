@@ -999,6 +999,21 @@ int oracle_score(const or_grid* g, int mode, int clip, const double* xyz, int na
     return 0;
 }
 
+// One atom's term of Eq. 1 (grid units) in score mode `mode` with its parity
+// band: out3 = (D, lo, hi), the term and the ends of its interval over the
+// voxel-boundary alternatives within `delta` grid units (nearest mode);
+// flags bit0 inside the box, bit1 some alternative disagrees on inside/outside
+// (the box band), bit2 lo < hi. For hand checks of the parity bands.
+int oracle_term(const or_grid* g, int mode, int clip, const double* x, double delta, double* out3, int* flags) {
+    Grid G{g, {g->nx, g->ny, g->nz}};
+    Term t = term(G, mode, V3{x[0], x[1], x[2]}, clip != 0, delta);
+    out3[0] = t.D;
+    out3[1] = t.lo;
+    out3[2] = t.hi;
+    *flags = (t.inbox ? 1 : 0) | (t.box_amb ? 2 : 0) | (t.score_amb ? 4 : 0);
+    return 0;
+}
+
 // Rodrigues rotation of natoms points about the axis through c along k (unit
 // vector computed here) by theta radians.
 void oracle_rotate(const double* xyz, int natoms, const double* c, const double* b, double theta, double* out) {

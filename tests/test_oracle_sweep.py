@@ -363,7 +363,7 @@ def test_peels_sit_at_tile_centres():
     kn.update(enable_refinement=1, n_poses=1, clip_box=0, bump_thr=0.0)
     opk = oracle.OraclePocket(pk)
     r = oracle.dock(opk, b, kn, trace=True, xyz_out=True)
-    x = oracle.peel_tile(2.0)  # 30 degrees
+    x = oracle.peel_tile(2.0)  # 24 degrees
     X = r["init_xyz"].reshape(-1, 3)
     x0, bonds, rot = indep.ligand(b, 0)
     moving, c, bb = indep.sides(len(x0), bonds, rot)[0]
