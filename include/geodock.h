@@ -336,23 +336,33 @@ int dock_measure_peaks(dock_ctx* ctx, int pocket_id, dock_peaks* out, void* stre
  * or arena and is capped there, or a caller that cannot afford the device
  * synchronisation an allocation or a free may bring. dock_run may allocate
  * its scratch on first use or when a batch grows; this call never does. Its
- * scratch (work-queue head, angle tables, pocket descriptor, task list,
- * per-pose keys and coordinates) lives in one file-scope device array of
- * about 51 MiB, which every GPU that loads the library holds until the
- * process exits.
+ * scratch (work-queue head, angle tables, task list, per-pose keys and
+ * coordinates) lives in one file-scope device array of about 50 MiB, which
+ * every GPU that loads the library holds until the process exits.
  *
- * Same docking as dock_run on ONE pocket, same results; the batch and pocket
- * must already be uploaded (dock_upload_ligands and dock_init_pocket do
- * allocate; do them at set-up). Outputs are device memory, written in stream
- * order on `stream`; the call does not wait for them.
+ * Same docking as dock_run on ONE pocket, with results equal to dock_run's
+ * bit for bit in every score mode when both run the same tile shape (the
+ * default, or the one dock_set_tile forces; a shape found by dock_autotune is
+ * not used here). The batch and pocket must already be uploaded
+ * (dock_upload_ligands and dock_init_pocket do allocate; do them at set-up).
+ * The call enqueues its kernels on `stream` and returns without waiting:
+ * outputs are device memory written in stream order, and no host memory is
+ * read once the call has returned (the angle tables travel as kernel
+ * parameters; the step choice of Alg. 2 is made on the device).
  *   out      device array of n dock_result (n = ligands in the batch)
  *   xyz_out  NULL or device array of 3*atom_off[n] floats (best pose, Å)
  * Limits per call: n_poses * n <= 131072 and n_poses * atom_off[n] <=
  * 4194304, and at most 361 angles per sweep; larger runs fail with
  * DOCK_ERR_INVALID_ARG before anything is launched.
+ * Cost: the work list runs in ligand order rather than longest first, and
+ * every ligand gets as many pose groups as the batch's largest ligand needs
+ * (the extra ones idle), so on batches of mixed sizes it is slower than
+ * dock_run.
  * The first call on a device looks up the array's device address there (once
  * per device, with that device current); make that first call before any
- * stream capture. Every call shares the one array and leaves its contents
+ * stream capture. The address stays valid for the life of the device's
+ * context: after cudaDeviceReset, do not call this entry point again in the
+ * same process. Every call shares the one array and leaves its contents
  * behind: the call clears what must start at zero itself, and calls whose
  * work overlaps on the GPU (other streams, other threads) race on it; keep
  * them ordered. dock_last_stats is not updated by this call. */

@@ -25,8 +25,25 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libgeodock.so")
 
 
+# geodock_sweep_inst.cu holds the sweep kernel's launchers for one angle-chunk size; it is compiled once
+# per size (one object each, in parallel)
+INST = os.path.join(CSRC, "geodock_sweep_inst.cu")
+CHUNK_SIZES = (8, 12, 18, 36)
+
+
 def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+
+
+def _units():
+    """(source, object name, extra nvcc flags) of every translation unit."""
+    out = []
+    for src in _sources():
+        if src == INST:
+            out += [(src, f"geodock_sweep_kc{kc}.o", [f"-DGD_KC={kc}"]) for kc in CHUNK_SIZES]
+        else:
+            out.append((src, os.path.basename(src) + ".o", []))
+    return out
 
 
 def _deps():
@@ -47,20 +64,21 @@ def build(force: bool = False, ptxas_verbose: bool = False, jobs: int | None = N
     cc = nvcc()
     objdir = os.path.join(HERE, "_build")
     os.makedirs(objdir, exist_ok=True)
-    srcs = _sources()
+    units = _units()
     extra = ["-Xptxas", "-v"] if ptxas_verbose else []
 
-    def compile_one(src):
-        obj = os.path.join(objdir, os.path.basename(src) + ".o")
-        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+    def compile_one(unit):
+        src, name, flags = unit
+        obj = os.path.join(objdir, name)
+        cmd = [cc, *ARCH, *FLAGS, *flags, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
-            raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
+            raise RuntimeError(f"nvcc failed on {src} {' '.join(flags)}:\n{r.stdout}\n{r.stderr}")
         return obj, r.stderr
 
-    jobs = jobs or min(len(srcs), os.cpu_count() or 4)
+    jobs = jobs or min(len(units), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(jobs) as ex:
-        results = list(ex.map(compile_one, srcs))
+        results = list(ex.map(compile_one, units))
     if ptxas_verbose:
         for _, log in results:
             sys.stderr.write(log)

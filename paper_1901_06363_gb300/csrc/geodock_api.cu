@@ -1599,10 +1599,13 @@ int dock_autotune(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs* 
 // ======================================================== static-scratch run
 //
 // dock_run_static: the batched sweep with its scratch (work-queue head, angle
-// tables, pocket descriptor, task list, per-pose keys and coordinates) taken
-// from one file-scope device array instead of allocated memory. The array is
-// created when the library's module is loaded on a device and held there
-// until the process exits, whether or not this entry point is ever called.
+// tables, task list, per-pose keys and coordinates) taken from one file-scope
+// device array instead of allocated memory. The array is created when the
+// library's module is loaded on a device and held there until the process
+// exits, whether or not this entry point is ever called. Nothing of the call
+// goes through host memory after it is enqueued: the angle tables travel as
+// kernel parameters, the pocket descriptor is the one dock_init_pocket left
+// on the device, and the step choice of Alg. 2 is made in the sweep kernel.
 
 namespace {
 
@@ -1612,14 +1615,11 @@ constexpr int kStaticAngles = 361;                       // angles per table (1 
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t kOffCounter = 0;
-constexpr size_t kOffPocket = 256;
-constexpr size_t kOffTables = kOffPocket + align256(sizeof(PocketDev));
+constexpr size_t kOffTables = 256;
 constexpr size_t kOffTasks = kOffTables + align256(3 * kStaticAngles * sizeof(float2));
 constexpr size_t kOffKeys = kOffTasks + align256(kStaticPoseSlots * sizeof(int2));
 constexpr size_t kOffXyz = kOffKeys + align256(kStaticPoseSlots * sizeof(unsigned long long));
-constexpr int64_t kStaticSides = int64_t(1) << 20;  // sweep descriptors whose step choice is staged per call
-constexpr size_t kOffCoarse = kOffXyz + align256(kStaticAtomPoses * 3 * sizeof(float));
-constexpr size_t kStaticBytes = kOffCoarse + align256(kStaticSides);  // about 51 MiB
+constexpr size_t kStaticBytes = kOffXyz + align256(kStaticAtomPoses * 3 * sizeof(float));  // about 50 MiB
 
 }  // namespace
 
@@ -1628,7 +1628,8 @@ static __device__ __align__(256) unsigned char g_dock_scratch[kStaticBytes];
 namespace {
 
 // Device address of g_dock_scratch on each device, looked up once per device
-// (with that device current) on the first call there.
+// (with that device current) on the first call there. It stays valid for the
+// life of the device's primary context.
 std::mutex g_static_mu;
 void* g_static_addr[256] = {};
 
@@ -1645,14 +1646,33 @@ cudaError_t static_scratch(int device, unsigned char** out) {
     return cudaSuccess;
 }
 
-// Work list in (pocket-ligand pair, pose group) order, one lanes-per-pose
-// (2^lq) for the whole batch.
-__global__ void static_tasks_kernel(int2* tasks, int npairs, int ngroup, int lq) {
+// The run's angle tables (cos, sin) by value: hp, lp and tile centres.
+struct StaticTables {
+    float2 t[3][kStaticAngles];
+};
+
+// Set-up of one call, in stream order before the sweep: the queue head to
+// zero, the angle tables into the array, and the work list in (pocket-ligand
+// pair, pose group) order with each ligand's lanes per pose chosen as the
+// batched form chooses them (the smallest power of two >= lq0 whose pose
+// group of 32 >> lq poses fits the warp's coordinate slice). Every ligand
+// gets ngroup slots; a group past its ligand's poses is an idle task.
+__global__ void static_setup_kernel(const __grid_constant__ StaticTables tabs, unsigned* counter, float2* tab_out,
+                                    int2* tasks, const LigDev* lig, int nlig, int ngroup, int lq0, int slice) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < (int64_t)npairs * ngroup) tasks[t] = make_int2((int)(t / ngroup), (int)(t % ngroup) | (lq << 16));
+    if (t == 0) *counter = 0u;
+    if (t < 3 * kStaticAngles) tab_out[t] = tabs.t[t / kStaticAngles][t % kStaticAngles];
+    if (t < (int64_t)nlig * ngroup) {
+        const int b = (int)(t / ngroup), g = (int)(t % ngroup);
+        const int l = lig[b].l;
+        int lq = lq0;
+        while (lq < 5 && (32 >> lq) * l * 3 > slice) ++lq;
+        tasks[t] = make_int2(b, g | (lq << 16));
+    }
 }
 
-// cos/sin of the angles offset + i * stride (degrees), FP64 rounded to FP32.
+// cos/sin of the angles offset + i * stride (degrees), FP64 rounded to FP32
+// (the same values as the batched form's tables).
 void fill_table(float2* t, int n, double offset, double stride) {
     const double rad = 3.14159265358979323846 / 180.0;
     for (int i = 0; i < n; ++i) {
@@ -1692,16 +1712,18 @@ extern "C" int dock_run_static(dock_ctx* ctx, int batch_id, int pocket_id, const
     CK(static_scratch(ctx->device, &base));
     cudaStream_t s = (cudaStream_t)stream;
 
-    // tile shape: the forced fields of dock_set_tile over the default (results do not depend on it)
+    // tile shape: the forced fields of dock_set_tile over the default (an autotuned shape is not used)
     dock_tile t = default_tile(k);
     if (ctx->tile.lanes_per_pose) t.lanes_per_pose = ctx->tile.lanes_per_pose;
     if (ctx->tile.angles_per_chunk) t.angles_per_chunk = ctx->tile.angles_per_chunk;
     if (ctx->tile.warps_per_cta) t.warps_per_cta = ctx->tile.warps_per_cta;
     if (k->score_mode == 2) t.angles_per_chunk = 12;
     const int slice = slice_floats(t, B.lmax);
-    const int lq = lanes_log2(t, slice, B.lmax);  // sized for the largest ligand
-    const int G = 32 >> lq, W = t.warps_per_cta, block = 32 * W;
-    const int ngroup = (N + G - 1) / G;
+    int lq0 = 0;
+    while ((1 << lq0) < t.lanes_per_pose) ++lq0;
+    const int lq_max = lanes_log2(t, slice, B.lmax);  // the largest ligand has the fewest poses per warp
+    const int W = t.warps_per_cta, block = 32 * W;
+    const int ngroup = (N + (32 >> lq_max) - 1) / (32 >> lq_max);
     const int ntask = B.n * ngroup;
     const int bw = bump_words(k);
     const size_t smem = cta_smem(t, slice, bw);
@@ -1709,29 +1731,26 @@ extern "C" int dock_run_static(dock_ctx* ctx, int batch_id, int pocket_id, const
     CK(occupancy(t.angles_per_chunk, k->score_mode, k->clip_box, block, smem, &per_sm));
     if (per_sm < 1) return fail(ctx, DOCK_ERR_UNSUPPORTED, "dock_run_static: tile does not fit on an SM");
 
-    // angle tables and the pocket descriptor: host values copied into the array
-    float2 tabs[3][kStaticAngles];
-    fill_table(tabs[0], P_hp, 0.0, k->hp_step);
-    fill_table(tabs[1], P_lp, 0.0, k->lp_step);
-    if (n_tiles) fill_table(tabs[2], n_tiles, 0.5 * tile, (double)tile);
-    else tabs[2][0] = make_float2(1.f, 0.f);
-    const PocketDev pd = ctx->pockets[pocket_id].d;
-    CK(cudaMemcpyAsync(base + kOffTables, tabs, sizeof tabs, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(base + kOffPocket, &pd, sizeof pd, cudaMemcpyHostToDevice, s));
-    // the queue head must start at zero; every other word is written before it is read
-    CK(cudaMemsetAsync(base + kOffCounter, 0, sizeof(unsigned), s));
-    if (ntask > 0) {
-        static_tasks_kernel<<<(ntask + 255) / 256, 256, 0, s>>>(reinterpret_cast<int2*>(base + kOffTasks), B.n, ngroup,
-                                                                lq);
-        CK(cudaGetLastError());
-    }
+    // set-up in stream order: queue head, angle tables (kernel parameters), work list
+    StaticTables tabs;
+    fill_table(tabs.t[0], P_hp, 0.0, k->hp_step);
+    fill_table(tabs.t[1], P_lp, 0.0, k->lp_step);
+    if (n_tiles) fill_table(tabs.t[2], n_tiles, 0.5 * tile, (double)tile);
+    else tabs.t[2][0] = make_float2(1.f, 0.f);
+    float2* tab = reinterpret_cast<float2*>(base + kOffTables);
+    const int64_t nset = std::max<int64_t>(3 * kStaticAngles, ntask);
+    static_setup_kernel<<<(unsigned)((nset + 255) / 256), 256, 0, s>>>(
+        tabs, reinterpret_cast<unsigned*>(base + kOffCounter), tab, reinterpret_cast<int2*>(base + kOffTasks), B.d_lig,
+        B.n, ngroup, lq0, slice);
+    CK(cudaGetLastError());
 
+    const PocketDev* pdev = ctx->pockets[pocket_id].dev->as<PocketDev>();
     SweepParams P{};
     P.lig = B.d_lig;
     P.side = B.d_side;
     P.idx = B.d_idx;
     P.xyz0 = B.d_xyz0;
-    P.pockets = reinterpret_cast<const PocketDev*>(base + kOffPocket);
+    P.pockets = pdev;
     P.tasks = reinterpret_cast<const int2*>(base + kOffTasks);
     P.ntask = ntask;
     P.nlig = B.n;
@@ -1742,20 +1761,9 @@ extern "C" int dock_run_static(dock_ctx* ctx, int batch_id, int pocket_id, const
     P.slice = slice;
     P.bw = bw;
     P.threshold = k->threshold;
-    if (B.nside_total <= kStaticSides) {
-        // Alg. 2's step choice per sweep descriptor, decided on the host (else in the kernel)
-        std::vector<uint8_t> co(std::max(1, B.nside_total), 0);
-        for (int b = 0; b < B.n; ++b)
-            for (int si = 0; si < B.nside[b]; ++si) {
-                const int g = B.side_off[b] + si;
-                co[g] = (double)B.side_m[g] / (double)B.l[b] <= k->threshold ? 1 : 0;
-            }
-        CK(cudaMemcpyAsync(base + kOffCoarse, co.data(), co.size(), cudaMemcpyHostToDevice, s));
-        P.coarse = base + kOffCoarse;
-    }
+    P.coarse = nullptr;  // Alg. 2's step choice per sweep in the kernel (the same FP64 test as on the host)
     P.bump_thr = k->bump_thr;
     P.seed = k->seed;
-    const float2* tab = reinterpret_cast<const float2*>(base + kOffTables);
     P.cs_hp = tab;
     P.cs_lp = tab + kStaticAngles;
     P.P_hp = P_hp;
@@ -1778,7 +1786,7 @@ extern "C" int dock_run_static(dock_ctx* ctx, int batch_id, int pocket_id, const
         FinalParams F{};
         F.pair0 = 0;
         F.lig = P.lig;
-        F.pockets = P.pockets;
+        F.pockets = pdev;
         F.pose_key = P.pose_key;
         F.pose_xyz = P.pose_xyz;
         F.npairs = B.n;

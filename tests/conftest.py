@@ -19,6 +19,11 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 def pytest_terminal_summary(terminalreporter):
     """Counts of the replay parity checks run in this session (candidates, band members, flips, differing
     choices and why, the largest final-coordinate deviation), so that a quiet run still shows them."""
+    w = terminalreporter.write_line
+    ref = sys.modules.get("test_gpu_refine")
+    worst = getattr(ref, "WORST", None)
+    if worst:
+        w(f"gradient checks: {len(worst)} comparisons, worst entry at {max(worst):.3f} of its tolerance")
     parity = sys.modules.get("parity")
     rec = getattr(parity, "RECORD", None)
     if not rec:
@@ -26,7 +31,6 @@ def pytest_terminal_summary(terminalreporter):
     keys = ("candidates", "amb_score", "amb_bump", "amb_box", "flips", "interval_used", "choice_differs",
             "choice_tie", "choice_overlap", "choice_flip")
     tot = {k: sum(s[k] for _, s in rec) for k in keys}
-    w = terminalreporter.write_line
     w(f"parity replays: {len(rec)} checks")
     for label, s in rec:
         if label:

@@ -193,12 +193,17 @@ def test_bench_workload_sampled(dk):
         d0 = np.linalg.norm(b.xyz[a0:a1][bonds[:, 0]] - b.xyz[a0:a1][bonds[:, 1]], axis=1)
         d1 = np.linalg.norm(xyz[0, a0:a1][bonds[:, 0]] - xyz[0, a0:a1][bonds[:, 1]], axis=1)
         assert np.allclose(d0, d1, atol=2e-3)
-    # sampled ligands: the same ligands (same ids) traced alone give the same results, and replay against the oracle
-    sample = np.array([0, 17, 333, 511, 700, 1023])
-    sub = b.subset(sample)
+    # 256 sampled ligands (a quarter of the batch, in four groups of 64): the same ligands (same ids) traced
+    # alone give the same results as the full launch, and replay candidate by candidate against the oracle
+    sample = np.sort(np.random.default_rng(2).choice(b.n, 256, replace=False))
     opk = oracle.OraclePocket(pks[0])
-    _, g, res_sub = trace_parity(dk, pks[0], sub, kn, opk=opk, ids=sample)
-    assert np.array_equal(res_sub.view(np.int32), res[sample].view(np.int32))
+    tot = 0
+    for part in np.split(sample, 4):
+        sub = b.subset(part)
+        stats, g, res_sub = trace_parity(dk, pks[0], sub, kn, opk=opk, ids=part)
+        assert np.array_equal(res_sub.view(np.int32), res[part].view(np.int32))
+        tot += stats["candidates"]
+    assert tot > 10_000_000
     dk.release_batch(bid)
 
 

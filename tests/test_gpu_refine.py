@@ -1,10 +1,14 @@
 """Parity of the refinement stage and the differentiable score (CUDA, through the C ABI) with the FP64 oracle.
 
-Tolerances: gradients within 1e-3 relative (per ligand, in the 2-norm) of the
-FP64 oracle gradient and of FP64 central differences; scores within 1e-4
-relative; poses within 1e-3 Å RMSD. The refinement is compared by replay: the
-oracle commits the GPU's accept decisions and every step's gradient, trial
-score and verdict are checked at the shared state.
+Tolerances: every gradient entry within 1e-3 relative of the FP64 oracle
+gradient and of FP64 central differences, |g_k - o_k| <= 1e-3 |o_k| + FLOOR *
+max_k |o_k|, where the floor (2e-5 of the ligand's largest entry) only matters
+for entries near zero: an entry is a sum of per-atom terms of up to the
+largest entry's size, so the FP32 sum of a few dozen of them carries an
+absolute rounding error of about 1e-6 of that size, whatever the entry's own
+value. Scores within 1e-4 relative; poses within 1e-3 Å RMSD. The refinement
+is compared by replay: the oracle commits the GPU's accept decisions and
+every step's gradient, trial score and verdict are checked at the shared state.
 """
 import numpy as np
 import pytest
@@ -16,8 +20,11 @@ import synth.configs as C
 pytestmark = pytest.mark.gpu
 
 REL_G = 1e-3
+FLOOR = 2e-5  # absolute floor per gradient entry, as a fraction of the ligand's largest entry
 REL_S = 1e-4
 RMSD = 1e-3
+AMB_BUMP = 4e-4  # Å^2 band around bump_thr^2, as in the sweep's replay
+WORST = []  # worst entry ratio of every gradient comparison (<= 1 passes)
 
 
 @pytest.fixture(scope="module")
@@ -52,8 +59,14 @@ def _near_face(opk, x, delta=1e-3):
     return bool(np.any(np.abs(t - np.round(t)) <= delta))
 
 
-def _rel(a, b):
-    return np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30)
+def _elem(a, b):
+    """Worst entry of |a_k - b_k| / (REL_G |b_k| + FLOOR max|b|): at most 1 when every entry agrees."""
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    tol = REL_G * np.abs(b) + FLOOR * max(np.abs(b).max(), 1e-30)
+    r = float((np.abs(a - b) / tol).max())
+    WORST.append(r)
+    return r
 
 
 def test_score_and_adjoint_match_oracle(env):
@@ -76,7 +89,7 @@ def test_score_and_adjoint_match_oracle(env):
             if _near_face(opk, x32[a0:a1]):
                 continue  # one-sided gradient on a cell face
             want = float(go[i]) * (-l / (pk.h ** 2 * S * S)) * dS
-            assert _rel(g[a0:a1], want) <= REL_G
+            assert _elem(g[a0:a1], want) <= 1, i
 
 
 def test_dof_apply_and_adjoint_match_oracle(env):
@@ -103,7 +116,7 @@ def test_dof_apply_and_adjoint_match_oracle(env):
         zo = oracle.dof_apply(b, i, x[a0:a1], q[i, :6 + T])
         assert np.abs(z[a0:a1] - zo).max() <= 1e-4
         Go = oracle.dof_grad(b, i, x[a0:a1], q[i, :6 + T], p[a0:a1])
-        assert _rel(G[i, :6 + T], Go) <= REL_G
+        assert _elem(G[i, :6 + T], Go) <= 1, i
         assert np.all(G[i, 6 + T:] == 0)
 
 
@@ -129,9 +142,10 @@ def test_autograd_pose_score_gradient(env):
             continue  # one-sided gradient on a cell face
         S, dS, inside = oracle.trilinear_grad(opk, x32[a0:a1])
         Go = oracle.dof_grad(b, i, x32[a0:a1], np.zeros(6 + T), -l / (pk.h ** 2 * S * S) * dS)
-        assert _rel(G[i, :6 + T], Go) <= REL_G
+        assert _elem(G[i, :6 + T], Go) <= 1, i
         # FP64 central differences (h = 1e-4) where no atom crosses a cell face
         eps = 1e-4
+        fmax = np.abs(Go).max()
         for k in range(6 + T):
             e = np.zeros(6 + T)
             e[k] = eps
@@ -142,7 +156,8 @@ def test_autograd_pose_score_gradient(env):
                 continue
             fd = (l / (pk.h ** 2 * oracle.score(opk, zp, mode=1)[0]) -
                   l / (pk.h ** 2 * oracle.score(opk, zm, mode=1)[0])) / (2 * eps)
-            assert abs(G[i, k] - fd) <= REL_G * np.abs(Go).max() + 1e-3 * abs(fd)
+            assert abs(G[i, k] - fd) <= REL_G * abs(fd) + FLOOR * fmax, (i, k)
+            WORST.append(abs(G[i, k] - fd) / (REL_G * abs(fd) + FLOOR * fmax))
             checked += 1
     assert checked >= 20
 
@@ -163,7 +178,7 @@ def _replay_check(b, kn, g, orc, xyz_start):
             if orc["flags"][k] & 8:
                 stats["face"] += 1  # one-sided gradient: the oracle took the GPU's direction
             else:
-                assert _rel(Gg, Go) <= REL_G, (i, s)
+                assert _elem(Gg, Go) <= 1, (i, s)
                 assert g["D"][k] == pytest.approx(orc["D"][k], rel=REL_G)
             if g["D"][k] > 0:
                 assert g["S_new"][k] == pytest.approx(orc["S_new"][k], rel=REL_S)
@@ -191,7 +206,7 @@ def test_refine_replay_parity(env):
     kn = C.knobs(refine_steps=20)
     g = d.refine_trace(bid, pid, kn, xyz)
     orc = oracle.refine(opk, b, xyz.astype(np.float32).astype(np.float64), steps=20, force_accept=g["accept"], force_G=g["G"],
-                        amb_delta=1e-3, amb_bump=2e-3, amb_rel=REL_S)
+                        amb_delta=1e-3, amb_bump=AMB_BUMP, amb_rel=REL_S)
     st = _replay_check(b, kn, g, orc, xyz)
     assert st["accepted"] > 20
     # the device-memory form returns the same results
@@ -216,7 +231,7 @@ def test_refine_edge_cases(env):
         for kn in (C.knobs(refine_steps=12), C.knobs(refine_steps=0), C.knobs(refine_steps=12, clip_box=0)):
             g = d.refine_trace(bid, pid, kn, x)
             orc = oracle.refine(opk, b, x.astype(np.float32).astype(np.float64), steps=kn["refine_steps"],
-                                clip=kn["clip_box"], force_accept=g["accept"], force_G=g["G"], amb_delta=1e-3, amb_bump=2e-3,
+                                clip=kn["clip_box"], force_accept=g["accept"], force_G=g["G"], amb_delta=1e-3, amb_bump=AMB_BUMP,
                                 amb_rel=REL_S)
             _replay_check(b, kn, g, orc, x)
         far = x + np.array([100.0, 0, 0])
@@ -242,14 +257,16 @@ def test_differentiation_workload_sampled(env):
     o0 = d.score_trilinear(bid, pid, xin).cpu().numpy()
     assert np.all(ref >= o0 * (1 - 1e-6))
     assert np.mean(ref > o0) > 0.5
-    # sampled ligands replayed against the oracle
-    sample = np.array([0, 1234, 4095])
+    # 256 sampled ligands replayed step by step against the oracle
+    sample = np.sort(np.random.default_rng(4).choice(b.n, 256, replace=False))
     sub = b.subset(sample)
     opk = oracle.OraclePocket(pks[0])
     bs = d.upload_ligands(sub, ids=sample)
     xs = np.concatenate([xyz[0, b.atom_off[i]:b.atom_off[i + 1]] for i in sample]).astype(np.float64)
     g = d.refine_trace(bs, pid, kn, xs)
-    orc = oracle.refine(opk, sub, xs, steps=20, force_accept=g["accept"], force_G=g["G"], amb_delta=1e-3, amb_bump=2e-3,
-                        amb_rel=REL_S)
-    _replay_check(sub, kn, g, orc, xs)
-    assert np.allclose(g["result"]["score"], ref[sample], rtol=0, atol=0)
+    orc = oracle.refine(opk, sub, xs, steps=20, force_accept=g["accept"], force_G=g["G"], amb_delta=1e-3,
+                        amb_bump=AMB_BUMP, amb_rel=REL_S)
+    st = _replay_check(sub, kn, g, orc, xs)
+    assert st["steps"] == 256 * 20 and st["accepted"] > 256
+    assert np.array_equal(g["result"]["score"], ref[sample])
+    print(f"refinement replay: {st}; worst gradient entry ratio {max(WORST):.3f} over {len(WORST)} comparisons")

@@ -48,17 +48,18 @@ def test_multi_pocket_grouped_launch(dk):
     assert np.all((res["pose"][ok] >= 0) & (res["pose"][ok] < kn["n_poses"])) and np.all(res["pose"][~ok] == -1)
     assert ok.mean() > 0.9
     dk.release_batch(bid)
-    # sampled ligands of every pocket replayed against the oracle; the grouped launch equals the single-pocket one
+    # 16 sampled ligands of every pocket (256 pairs) replayed against the oracle; the grouped launch equals the
+    # single-pocket one
     rng = np.random.default_rng(5)
-    sample = np.sort(rng.choice(b.n, 2, replace=False))
     for i, (pk, pid) in enumerate(zip(pks, pids)):
+        sample = np.sort(rng.choice(b.n, 16, replace=False))
         _replay_sample(dk, pk, pid, b, kn, sample, res[i][sample])
 
 
 def test_knob_sweep_combinations(dk):
-    """The 45 (step, poses, repetitions) combinations on 2,048 lognormal ligands; sampled ligands replayed."""
-    pks, _, combos = C.knob_sweep(n=1)
-    b = C.sweep_batch(2048)
+    """The 45 (step, poses, repetitions) combinations on the 100,000 lognormal ligands; 6 sampled ligands of
+    every combination (270) replayed against the oracle."""
+    pks, b, combos = C.knob_sweep()
     pid = dk.init_pocket(pks[0])
     bid = dk.upload_ligands(b)
     natoms = int(b.atom_off[-1])
@@ -74,8 +75,9 @@ def test_knob_sweep_combinations(dk):
         assert m[0] <= m[1] <= m[2]
         m = [np.mean(best[(s, 32, r)]["score"]) for r in C.SWEEP_REPS]
         assert m[0] <= m[1] * (1 + 1e-6) and m[1] <= m[2] * (1 + 1e-6)
-    sample = np.array([3, 1500])
-    for (s, p, r) in [(5.0, 8, 1), (45.0, 128, 1), (20.0, 32, 4), (10.0, 8, 16)]:
-        kn = [k for k in combos if (k["hp_step"], k["n_poses"], k["repetitions"]) == (s, p, r)][0]
-        _replay_sample(dk, pks[0], pid, b, kn, sample, best[(s, p, r)][sample])
+    rng = np.random.default_rng(3)
+    for kn in combos:
+        sample = np.sort(rng.choice(b.n, 6, replace=False))
+        key = (kn["hp_step"], kn["n_poses"], kn["repetitions"])
+        _replay_sample(dk, pks[0], pid, b, kn, sample, best[key][sample])
     dk.release_batch(bid)
