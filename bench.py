@@ -151,6 +151,221 @@ def cpu_baseline(pk, batch, kn, target_s=12.0):
             "sample": f"first {done} of the {batch.n} workload ligands, all 64 poses each ({elapsed:.1f} s)"}
 
 
+def sweep_nmov(batch):
+    """Moving atoms (the fragment minus its bond atom) of every fragment sweep of each ligand, in sweep order
+    (per rotatable bond: the left fragment, then the right one; Alg. 1)."""
+    from paper_1901_06363_gb300 import shard
+    l, _ = batch.sizes()
+    out = []
+    for b, left in enumerate(shard.fragment_sizes(batch)):
+        out.append(np.array([v for m in left for v in (m - 1, int(l[b]) - m - 1)], np.int64))
+    return out
+
+
+def feasible_work(dk, bid, pid, kn, batch):
+    """Exact work counts of the batched run, from a traced run of the same batch and knobs: the trace records
+    every repetition, and those after a pose's first repetition without a commit (a fixed point, which the
+    batched run does not compute) are dropped here. Returns evaluated and feasible candidates, and their
+    moving-atom lookups (Alg. 1 scores only the feasible candidates)."""
+    import torch
+    bufs, _, pmax, _ = dk.run_trace_device(bid, pid, kn, batch)
+    N, R = int(kn["n_poses"]), int(kn["repetitions"])
+    _, t = batch.sizes()
+    nsw = R * 2 * t.astype(np.int64)
+    total = int((nsw * N).sum())
+    st = bufs["cand_status"][:total * pmax].view(total, pmax)[:, 1:]
+    feas = (st == 1).sum(1).cpu().numpy()
+    ev = (st != -2).sum(1).cpu().numpy()
+    ck = bufs["chosen_k"][:total].cpu().numpy()
+    live = bufs["pose_status"][:batch.n * N].cpu().numpy() == 0
+    del bufs, st
+    torch.cuda.empty_cache()
+    nmov = sweep_nmov(batch)
+    c = dict(candidates=0, feasible=0, lookups=0, feasible_lookups=0)
+    s0 = 0
+    for b in range(batch.n):
+        ns = int(t[b]) * 2
+        n = N * R * ns
+        if ns == 0 or R == 0:
+            continue
+        moved = (ck[s0:s0 + n].reshape(N, R, ns) != 0).any(2)
+        still = ~moved
+        first = np.where(still.any(1), still.argmax(1), R - 1)
+        comp = (np.arange(R)[None, :] <= first[:, None]) & live[b * N:(b + 1) * N, None]
+        m = np.broadcast_to(comp[:, :, None], (N, R, ns)).ravel()
+        w = np.tile(nmov[b], N * R)
+        f, e = feas[s0:s0 + n][m], ev[s0:s0 + n][m]
+        c["candidates"] += int(e.sum())
+        c["feasible"] += int(f.sum())
+        c["lookups"] += int((e * w[m]).sum())
+        c["feasible_lookups"] += int((f * w[m]).sum())
+        s0 += n
+    return c
+
+
+def roofline_8d(st, fw, sweep_s, rates, traffic, hbm_gbs):
+    """Roofline of the sweep kernel by the algorithmic work per pose-eval (candidate): FP32 operations
+    6 m (rotation) + (m - 1)(l - m - 1) x 3 (bump test, every pair at every candidate: 2 FMA + 1 compare) +
+    m (score adds) + 1 (the division), counted as lane operations at the measured FMA rate; field gathers
+    m per feasible candidate at the measured texture-fetch rate; HBM bytes at the copy bandwidth. The bound is
+    the resource whose time at its peak is largest; frac = that time / the measured kernel time."""
+    placements = st["atom_updates"] + st["lookups_skipped"]
+    fp32 = 7.0 * placements + 3.0 * st["bump_pairs"] + st["candidates"]
+    t_fp32 = fp32 / rates["fma_per_s"]
+    t_tex = fw["feasible_lookups"] / rates["tex_local_per_s"]
+    t_hbm = (traffic or 0) / (hbm_gbs * 1e9)
+    res = {
+        "fp32": {"work": fp32, "unit": "lane-ops", "peak": rates["fma_per_s"], "time_s": t_fp32,
+                 "achieved": fp32 / sweep_s, "frac": t_fp32 / sweep_s},
+        "texture": {"work": fw["feasible_lookups"], "unit": "fetches", "peak": rates["tex_local_per_s"],
+                    "time_s": t_tex, "achieved": fw["feasible_lookups"] / sweep_s, "frac": t_tex / sweep_s},
+        "hbm": {"work": traffic, "unit": "bytes", "peak": hbm_gbs * 1e9, "time_s": t_hbm,
+                "achieved": (traffic or 0) / sweep_s, "frac": t_hbm / sweep_s},
+    }
+    bound = max(res, key=lambda r: res[r]["time_s"])
+    return bound, res
+
+
+def _device_time(fn, torch, stream, reps=3):
+    """Median CUDA-event time (s) of fn() on `stream` over `reps` runs, after one warm-up run."""
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    return float(np.median(ts))
+
+
+def leg_single(dk, torch, stream):
+    """One ligand x one pocket (24 atoms, 4 rotatable bonds, 48^3, 8 poses, 10 degrees, 1 repetition)."""
+    import synth.configs as C
+    pks, b, kn = C.single()
+    pid = dk.init_pocket(pks[0])
+    bid = dk.upload_ligands(b)
+    natoms = int(b.atom_off[-1])
+    out = torch.empty(4, dtype=torch.int32, device="cuda")
+    xyz = torch.empty(natoms * 3, dtype=torch.float32, device="cuda")
+    t = _device_time(lambda: dk.run(bid, [pid], kn, 1, natoms, out=out, xyz_out=xyz, stream=stream), torch, stream, 20)
+    cand = dk.stats()["candidates"]
+    tp = _device_time(lambda: dk.run(bid, [pid], dict(kn, plain_mode=1), 1, natoms, out=out, xyz_out=xyz,
+                                     stream=stream), torch, stream, 20)
+    dk.release_batch(bid)
+    return {"workload": "1 ligand (24 atoms, 4 rotatable bonds) x 1 pocket 48^3, 8 poses, 10 deg, 1 rep",
+            "ligands_per_s": 1 / t, "pose_evals_per_s": cand / t, "atoms_per_s": natoms / t, "ms": 1e3 * t,
+            "plain_ligands_per_s": 1 / tp, "batched_vs_plain": tp / t,
+            "note": "one ligand: the batched form (one graph launch) against the plain form (its own launches)"}
+
+
+def leg_diff(dk, torch, stream, plain_n=64):
+    """4,096 ligands (20-60 atoms, 3-10 rotatable bonds) on a 64^3 trilinear field: sampled stage (64 poses,
+    10 degrees, 4 repetitions), then 20 refinement steps from each ligand's best pose."""
+    import synth.configs as C
+    pks, b, kn = C.differentiation()
+    pid = dk.init_pocket(pks[0])
+    bid = dk.upload_ligands(b)
+    n, natoms = b.n, int(b.atom_off[-1])
+    out = torch.empty(n * 4, dtype=torch.int32, device="cuda")
+    xyz = torch.empty(natoms * 3, dtype=torch.float32, device="cuda")
+    t_s = _device_time(lambda: dk.run(bid, [pid], kn, n, natoms, out=out, xyz_out=xyz, stream=stream), torch, stream)
+    cand = dk.stats()["candidates"]
+    rout = torch.empty(n * 4, dtype=torch.int32, device="cuda")
+    rxyz = torch.empty_like(xyz)
+    t_r = _device_time(lambda: dk.refine(bid, [pid], kn, xyz, out=rout, xyz_out=rxyz, stream=stream), torch, stream)
+    o0 = dk.score_trilinear(bid, pid, xyz)
+    gain = float((rout.view(torch.float32).reshape(-1, 4)[:, 0] / o0).mean().item())
+    dk.release_batch(bid)
+    sub = b.subset(np.arange(plain_n))
+    sb = dk.upload_ligands(sub, ids=np.arange(plain_n) + b.id_base)
+    sat = int(sub.atom_off[-1])
+    so = torch.empty(plain_n * 4, dtype=torch.int32, device="cuda")
+    sx = torch.empty(sat * 3, dtype=torch.float32, device="cuda")
+    tp = _device_time(lambda: dk.run(sb, [pid], dict(kn, plain_mode=1), plain_n, sat, out=so, xyz_out=sx,
+                                     stream=stream), torch, stream, 1)
+    dk.release_batch(sb)
+    return {"workload": "4096 ligands (20-60 atoms, 3-10 rotatable bonds) x 1 pocket 64^3 trilinear, 64 poses, "
+                        "10 deg, 4 reps, then 20 refinement steps",
+            "ligands_per_s": n / (t_s + t_r), "sampled_ligands_per_s": n / t_s, "refined_ligands_per_s": n / t_r,
+            "pose_evals_per_s": cand / t_s, "atoms_per_s": natoms / (t_s + t_r), "ms_sampled": 1e3 * t_s,
+            "ms_refined": 1e3 * t_r, "refined_over_sampled_score": gain,
+            "plain_ligands_per_s": plain_n / tp, "batched_vs_plain": (n / t_s) / (plain_n / tp),
+            "note": f"plain form of the sampled stage on the first {plain_n} ligands"}
+
+
+def leg_multi(dk, torch, stream, plain_pairs=64):
+    """16 pockets (48^3-128^3) x 50,000 lognormal ligands in one grouped launch; 32 poses, 15 deg, 2 reps."""
+    import synth.configs as C
+    pks, b, kn = C.multi_pocket()
+    pids = [dk.init_pocket(p) for p in pks]
+    bid = dk.upload_ligands(b)
+    n, natoms = b.n, int(b.atom_off[-1])
+    npk = len(pks)
+    out = torch.empty(npk * n * 4, dtype=torch.int32, device="cuda")
+    t = _device_time(lambda: dk.run(bid, pids, kn, n, natoms, out=out, xyz_out=None, stream=stream), torch, stream, 2)
+    cand = dk.stats()["candidates"]
+    dk.release_batch(bid)
+    # plain form: one launch per pair, on the first plain_pairs / 16 ligands of every pocket
+    k = plain_pairs // npk
+    sub = b.subset(np.arange(k))
+    sb = dk.upload_ligands(sub, ids=np.arange(k) + b.id_base)
+    so = torch.empty(npk * k * 4, dtype=torch.int32, device="cuda")
+    tp = _device_time(lambda: dk.run(sb, pids, dict(kn, plain_mode=1), k, int(sub.atom_off[-1]), out=so,
+                                     xyz_out=None, stream=stream), torch, stream, 1)
+    dk.release_batch(sb)
+    return {"workload": "16 pockets (48^3-128^3) x 50000 ligands (lognormal, median 32 atoms), 32 poses, 15 deg, "
+                        "2 reps, one grouped launch",
+            "ligands_per_s": n / t, "pairs_per_s": npk * n / t, "pose_evals_per_s": cand / t,
+            "atoms_per_s": npk * natoms / t, "s": t, "plain_pairs_per_s": npk * k / tp,
+            "batched_vs_plain": (npk * n / t) / (npk * k / tp),
+            "note": f"ligands_per_s counts a ligand once for all 16 pockets; plain form on {npk * k} pairs"}
+
+
+def leg_sweep(dk, torch, stream):
+    """The 100,000 lognormal ligands x the 64^3 pocket at one point of the knob grid (10 deg, 32 poses, 4 reps)."""
+    import synth.configs as C
+    pks, b, combos = C.knob_sweep()
+    kn = [c for c in combos if (c["hp_step"], c["n_poses"], c["repetitions"]) == (10.0, 32, 4)][0]
+    pid = dk.init_pocket(pks[0])
+    bid = dk.upload_ligands(b)
+    n, natoms = b.n, int(b.atom_off[-1])
+    out = torch.empty(n * 4, dtype=torch.int32, device="cuda")
+    t = _device_time(lambda: dk.run(bid, [pid], kn, n, natoms, out=out, xyz_out=None, stream=stream), torch, stream, 2)
+    cand = dk.stats()["candidates"]
+    dk.release_batch(bid)
+    return {"workload": "100000 ligands (lognormal, median 32 atoms, Poisson(6) rotatable bonds) x 1 pocket 64^3, "
+                        "10 deg, 32 poses, 4 reps (one point of the 45-point knob grid)",
+            "ligands_per_s": n / t, "pose_evals_per_s": cand / t, "atoms_per_s": natoms / t, "s": t}
+
+
+def cpu_configs(cores):
+    """The FP64 oracle on bounded samples of the other workloads (whole ligands, all poses), on the host cores."""
+    import oracle
+    import synth.configs as C
+    out = {}
+
+    def timed(name, pks, b, kn, idx, pairs=1):
+        opks = [oracle.OraclePocket(p) for p in pks]
+        sub = b.subset(idx)
+        t0 = time.perf_counter()
+        for opk in opks:
+            oracle.dock(opk, sub, kn, nthreads=cores, ids=idx + b.id_base)
+        dt = time.perf_counter() - t0
+        out[name] = {"ligands_per_s": len(idx) / dt, "pairs_per_s": len(idx) * len(opks) / dt,
+                     "sample": f"{len(idx)} ligands x {len(opks)} pocket(s), {dt:.1f} s"}
+
+    pks, b, kn = C.single()
+    timed("single", pks, b, kn, np.arange(1))
+    pks, b, kn = C.differentiation()
+    timed("differentiation", pks, b, kn, np.arange(2 * cores))
+    pks, b, kn = C.multi_pocket()
+    timed("multi_pocket", pks[::5], b, kn, np.arange(cores))
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -323,17 +538,48 @@ def run_ours(args):
     peaks, src = _peaks()
     f_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    # issue-slot roofline of the sweep kernel: 4 schedulers x 32 lanes per SM per clock
-    peak_inst = sms * 4 * 32 * f_mhz * 1e6 / 1e12
-    # algorithmic instructions per launch: 16 per (candidate, moving atom) field lookup
-    # (6 FMA rotation, 3 floor, 3 bound tests, 2 index, 1 load, 1 add) and 8 per circle
-    # bound test of the bump check (3 sub, 3 FMA, compare, vote)
-    inst = 16.0 * st["atom_updates"] + 8.0 * st["pair_bounds"]
     sweep_avg = statistics.mean(sweep_ms)
-    achieved = inst / (sweep_avg / 1e3) / 1e12
-    lookups_per_s = st["atom_updates"] / (sweep_avg / 1e3)
+    sweep_s = sweep_avg / 1e3
     clocks = clk.summary()
     rates = dk.measure_peaks(pid, stream=stream)  # after the timed region
+    # exact feasible-candidate counts of the timed launch (from a traced run of the same batch and knobs)
+    fw = feasible_work(dk, bid, pid, kn, batch)
+    traffic = _traffic()
+    bound, res = roofline_8d(st, fw, sweep_s, rates, traffic, float(peaks.get("hbm_gbs", 6800.0)))
+    rb = res[bound]
+    roofline = {"bound": bound, "achieved": rb["achieved"], "peak": rb["peak"],
+                "unit": {"texture": "fetches/s", "fp32": "lane-ops/s", "hbm": "B/s"}[bound], "frac": rb["frac"],
+                "traffic": traffic, "traffic_unit": "DRAM bytes per launch (ncu)", "kernel": "sweep_kernel",
+                "sweep_ms": sweep_avg, "feasible_fraction": fw["feasible"] / max(fw["candidates"], 1),
+                "peak_source": "texture: point-sampled fetches within 16^3-voxel cubes (the locality of one "
+                               "ligand's poses), the higher of the two fetch rates dock_measure_peaks measured in "
+                               "this run; fp32: its FMA rate; hbm: " + src + " copy bandwidth",
+                "resources": res,
+                "work": {"candidates": fw["candidates"], "feasible_candidates": fw["feasible"],
+                         "feasible_lookups": fw["feasible_lookups"], "placements": fw["lookups"],
+                         "lookups_done": int(st["atom_updates"]), "bump_pairs": int(st["bump_pairs"]),
+                         "counts_match_run": fw["candidates"] == st["candidates"] and
+                         fw["lookups"] == st["atom_updates"] + st["lookups_skipped"]}}
+    # issue-slot view of the same kernel (secondary): 16 lane instructions per lookup made and 8 per circle bound
+    peak_inst = sms * 4 * 32 * f_mhz * 1e6
+    inst = 16.0 * st["atom_updates"] + 8.0 * st["pair_bounds"]
+    issue = {"achieved": inst / sweep_s, "peak": peak_inst, "unit": "lane-instructions/s",
+             "frac": inst / sweep_s / peak_inst,
+             "note": f"{sms} SMs x 4 schedulers x 32 lanes x sm_max_mhz {f_mhz:.0f}; 16 per lookup made (6 FMA, 3 "
+                     "floor, 3 bound tests, 2 index, 1 load, 1 add), 8 per circle bound (3 sub, 3 FMA, compare, vote)"}
+    # the other workloads on this GPU (batched against plain), then the oracle on host cores
+    configs = {"single": leg_single(dk, torch, stream), "knob_sweep_point": leg_sweep(dk, torch, stream),
+               "differentiation": leg_diff(dk, torch, stream), "multi_pocket": leg_multi(dk, torch, stream)}
+    cpu = None
+    if world == 1:
+        cpu = cpu_baseline(pk, batch, kn)
+        t0 = time.perf_counter()
+        import oracle
+        one = batch.subset(np.arange(8))
+        oracle.dock(oracle.OraclePocket(pk), one, kn, nthreads=1, ids=np.arange(8) + batch.id_base)
+        dt = time.perf_counter() - t0
+        cpu["one_core"] = {"value": 8 / dt, "unit": UNIT, "cores": 1, "sample": f"first 8 workload ligands ({dt:.1f} s)"}
+        cpu["configs"] = cpu_configs(cpu["cores"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -345,18 +591,13 @@ def run_ours(args):
         "atoms_per_s": world * natoms * args.steps / total_s,
         "plain_ligands_per_s": world * n / plain_s,
         "batched_vs_plain": (value / world) / (n / plain_s),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_inst, "unit": "Tinst/s",
-                     "frac": achieved / peak_inst, "traffic": _traffic(), "traffic_unit": "bytes per launch (ncu)",
-                     "kernel": "sweep_kernel", "sweep_ms": sweep_avg,
-                     "peak_source": f"152 SMs x 128 lanes x sm_max_mhz {f_mhz:.0f} ({src} clocks)"},
+        "roofline": roofline,
+        "roofline_issue": issue,
         "measured_rates": rates,
-        "gather_roofline": {"bound": "texture fetches", "achieved": lookups_per_s, "peak": rates["tex_local_per_s"],
-                            "unit": "fetches/s", "frac": lookups_per_s / rates["tex_local_per_s"],
-                            "note": "field lookups done by the sweep per second of sweep time, against the "
-                                    "measured point-sampled fetch rate within 16^3-voxel cubes"},
+        "configs": configs,
         "refine": refine,
         "exact_score": exact,
-        "cpu_baseline": cpu_baseline(pk, batch, kn) if world == 1 else None,
+        "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clocks,
         "gpu_launches": int(st["kernel_launches"]) * args.steps,

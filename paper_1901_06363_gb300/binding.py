@@ -293,6 +293,16 @@ class Docker:
 
     def run_trace(self, bid: int, pid: int, kn, batch):
         """dock_run_trace: per-candidate trace (device buffers via torch), returned as numpy arrays."""
+        bufs, sizes, pmax, out = self.run_trace_device(bid, pid, kn, batch)
+        res = {name: tns.cpu().numpy()[:sizes[name]] for name, tns in bufs.items()}
+        res["pmax"] = pmax
+        res["result"] = out
+        return res
+
+    def run_trace_device(self, bid: int, pid: int, kn, batch):
+        """dock_run_trace into torch CUDA tensors, left on the device.
+
+        Returns (tensors by trace field, valid length of each, pmax, host results)."""
         import torch
         k = knobs_struct(kn)
         pmax = lib.dock_trace_pmax(ctypes.byref(k))
@@ -319,13 +329,10 @@ class Docker:
         rc = lib.dock_run_trace(self._c, bid, pid, ctypes.byref(k), ctypes.byref(tr), ctypes.c_void_p(out.ctypes.data),
                                 _stream_ptr(None))
         self._check(rc, "dock_run_trace")
-        res = {name: tns.cpu().numpy()[:{"chosen_k": total, "cand_S": total * pmax, "cand_status": total * pmax,
-                                          "pose_S": batch.n * N, "pose_init_S": batch.n * N,
-                                          "pose_status": batch.n * N, "init_xyz": natoms * N * 3,
-                                          "pose_xyz": natoms * N * 3}[name]] for name, tns in bufs.items()}
-        res["pmax"] = pmax
-        res["result"] = out
-        return res
+        sizes = {"chosen_k": total, "cand_S": total * pmax, "cand_status": total * pmax, "pose_S": batch.n * N,
+                 "pose_init_S": batch.n * N, "pose_status": batch.n * N, "init_xyz": natoms * N * 3,
+                 "pose_xyz": natoms * N * 3}
+        return bufs, sizes, pmax, out
 
     # ------------------------------------------------------------------ tiles
     def set_tile(self, lanes_per_pose=0, angles_per_chunk=0, warps_per_cta=0):

@@ -6,24 +6,72 @@ split by ligands with no data-path exchange: each rank docks its own shard
 with dock_run and only the per-pair results travel, gathered to rank 0.
 
 The split is a greedy longest-processing-time assignment on the work model
-of a ligand, n_poses * repetitions * sum over its fragment sweeps of
-candidates * moving atoms (the sweep's rotations and lookups): ligands in
-decreasing cost, each to the currently least-loaded rank. Ligand identity
-(hence its seeded initial poses) travels with it, so a sharded run returns
-exactly the results of an unsharded one.
+of a ligand: n_poses * repetitions * sum over its fragment sweeps of
+candidates * (moving atoms + PAIR_WEIGHT * moving-fixed atom pairs), the
+sweep's rotations and lookups plus its bump check; ligands in decreasing
+cost, each to the currently least-loaded rank. Ligand identity (hence its
+seeded initial poses) travels with it, so a sharded run returns exactly the
+results of an unsharded one.
 """
 from __future__ import annotations
 
 import numpy as np
 
+# Relative cost of one (moving, fixed) atom pair of the bump check against one moving-atom rotation and
+# lookup: the exact circle bound rejects most pairs at one test per sweep, and the rest cost a few FP32
+# operations per candidate, so a pair weighs a fraction of a lookup.
+PAIR_WEIGHT = 0.1
+
+
+def fragment_sizes(batch):
+    """Per ligand, the atom count of the side of each rotatable bond that holds its lower atom index
+    (Alg. 1's left fragment), from one depth-first search per ligand: removing a bridge splits a ligand into
+    the subtree below it and the rest."""
+    out = []
+    for b in range(batch.n):
+        a0, a1 = int(batch.atom_off[b]), int(batch.atom_off[b + 1])
+        l = a1 - a0
+        bonds = batch.bonds[batch.bond_off[b]:batch.bond_off[b + 1]]
+        adj = [[] for _ in range(l)]
+        for u, v in bonds:
+            adj[int(u)].append(int(v))
+            adj[int(v)].append(int(u))
+        parent = [-1] * l
+        order, seen, stack = [], [False] * l, [0]
+        seen[0] = True
+        while stack:
+            x = stack.pop()
+            order.append(x)
+            for y in adj[x]:
+                if not seen[y]:
+                    seen[y] = True
+                    parent[y] = x
+                    stack.append(y)
+        size = [1] * l
+        for x in reversed(order):
+            if parent[x] >= 0:
+                size[parent[x]] += size[x]
+        left = []
+        for e in batch.rot[batch.rot_off[b]:batch.rot_off[b + 1]]:
+            u, v = sorted(int(a) for a in bonds[int(e)])
+            below = v if parent[v] == u else u  # the bond's atom on the far side from atom 0
+            left.append(l - size[below] if below == v else size[below])
+        out.append(left)
+    return out
+
 
 def ligand_costs(batch, n_angles_hp: int, n_poses: int, repetitions: int) -> np.ndarray:
-    """Work model per ligand: poses x repetitions x sum over the 2T sweeps of (candidates x moving atoms)."""
-    l, t = batch.sizes()
+    """Work model per ligand: poses x repetitions x sum over the 2T sweeps of candidates x (moving atoms +
+    PAIR_WEIGHT x bump pairs). A bond whose sides hold m and l - m atoms gives the sweeps m - 1 and l - m - 1
+    moving atoms and (m - 1)(l - m - 1) bump pairs each."""
+    l, _ = batch.sizes()
     cost = np.zeros(batch.n)
-    for b in range(batch.n):
-        # each rotatable bond is swept twice (left, right); their moving sides sum to l - 2 moving atoms
-        cost[b] = (n_angles_hp - 1) * max(int(l[b]) - 2, 1) * max(int(t[b]), 0) + int(l[b])
+    for b, left in enumerate(fragment_sizes(batch)):
+        c = 0.0
+        for m in left:
+            r = int(l[b]) - m
+            c += (m - 1) + (r - 1) + PAIR_WEIGHT * 2 * (m - 1) * (r - 1)
+        cost[b] = (n_angles_hp - 1) * c + int(l[b])
     return cost * n_poses * max(repetitions, 1)
 
 

@@ -20,13 +20,16 @@ coordinates must agree within RMSD.
 
 Why these bands. The GPU works in FP32 grid units (coordinates below 2^8, an
 ulp of at most 2^-16) and commits each chosen angle by rounding; over a
-run's commits its coordinates drift from the oracle's FP64 ones by a few
-1e-5 grid units (the measured maximum is reported as max_dev_A). A nearest
-voxel can differ only for an atom that close to a voxel face (the band of
-1e-3 voxel holds it with room to spare); a squared distance near thr^2 =
-(2 Å)^2 moves by about 2 * 2 Å * 2 * drift plus the FP32 rounding of
-A + B cos + C sin (under 1e-5 Å^2), so a band of 4e-4 Å^2 covers a drift of
-up to 5e-5 Å per atom.
+run's commits its coordinates drift from the oracle's FP64 ones (the
+measured maximum is reported as max_dev_A: typically 2e-5 to 7e-5 Å at the
+end of a run, 1.4e-4 Å at most over the GPU suite). A nearest voxel can
+differ only for an atom that close to a voxel face, far inside the band of
+1e-3 voxel. A squared distance near thr^2 = (2 Å)^2 moves by at most about
+2 * 2 Å * (the drift of the pair's difference) plus the FP32 rounding of
+A + B cos + C sin (under 1e-5 Å^2): about 2e-4 Å^2 for a typical drift of
+5e-5 Å. The band of 4e-4 Å^2 is the parity protocol's; over the GPU suite's
+75 million compared candidates every feasibility difference lay inside it
+(the suite prints the counts).
 """
 from __future__ import annotations
 

@@ -25,6 +25,26 @@ def test_lpt_small_cases():
     assert [list(p) for p in shard.lpt_shards([1.0], 3)] == [[0], [], []]
 
 
+def test_fragment_sizes_and_costs():
+    import indep
+    import synth
+    l, t = synth.ligand_sizes(42, 40, 0, [10, 60, 0, 8])
+    b = synth.ligand_batch(42, l, t)
+    fs = shard.fragment_sizes(b)
+    for i in range(b.n):
+        x, bonds, rot = indep.ligand(b, i)
+        sides = indep.sides(len(x), bonds, rot)
+        assert fs[i] == [int(sides[2 * k][0].sum()) for k in range(len(rot))]
+    # the cost of a ligand: candidates x (moving atoms + weighted bump pairs) over its sweeps, per pose and repetition
+    c = shard.ligand_costs(b, 37, 4, 2)
+    for i in range(b.n):
+        want = 0.0
+        for m in fs[i]:
+            r = int(l[i]) - m
+            want += (m - 1) + (r - 1) + shard.PAIR_WEIGHT * 2 * (m - 1) * (r - 1)
+        assert c[i] == (36 * want + int(l[i])) * 4 * 2
+
+
 def _free_port():
     s = socket.socket()
     s.bind(("127.0.0.1", 0))
