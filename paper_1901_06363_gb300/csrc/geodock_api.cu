@@ -238,6 +238,20 @@ int peel_tile(double step) {
     return best;
 }
 
+// Angle counts of a run's knobs, computed once per call (peel_tile searches the divisors of 360, too slow
+// to repeat per ligand and sweep descriptor on large batches).
+struct Steps {
+    int P_hp = 1, P_lp = 1;
+    int tile = 0;  // tile of tile peeling, 0 without it
+};
+Steps steps_of(const dock_knobs* k) {
+    Steps s;
+    s.P_hp = n_angles(k->hp_step);
+    s.P_lp = n_angles(k->lp_step);
+    if (k->enable_refinement) s.tile = peel_tile(k->hp_step);
+    return s;
+}
+
 std::vector<float2> angle_table(const std::vector<double>& deg) {
     std::vector<float2> t(deg.size());
     const double rad = 3.14159265358979323846 / 180.0;
@@ -315,10 +329,14 @@ size_t cta_smem(const dock_tile& t, int slice, int bw) {
 // 64-bit bump words per lane: the largest phase of a sweep (flat hp or lp
 // sweep, tile centres, or one tile's angles) in 64-candidate words.
 int bump_words(const dock_knobs* k) {
-    int m = std::max(n_angles(k->hp_step), n_angles(k->lp_step)) - 1;
+    // with tile peeling a high-precision fragment sweeps the tile centres, then one tile: never the flat hp
+    // candidates
+    int m = n_angles(k->lp_step) - 1;
     if (k->enable_refinement) {
         int x = peel_tile(k->hp_step);
         m = std::max(m, std::max(360 / x, (int)std::lround(x / k->hp_step)));
+    } else {
+        m = std::max(m, n_angles(k->hp_step) - 1);
     }
     return std::max(1, (m + 63) / 64);
 }
@@ -353,17 +371,13 @@ std::string plan_key(int batch_id, const int32_t* pids, int np, const dock_knobs
 
 // Estimated cost of one warp task (pose group) of ligand b: candidate
 // evaluations times moving atoms, plus the bump partner scans per chunk.
-double task_cost(const BatchH& B, int b, const dock_knobs* k, int Q, int kc) {
-    int P_hp = n_angles(k->hp_step), P_lp = n_angles(k->lp_step);
+double task_cost(const BatchH& B, int b, const dock_knobs* k, const Steps& st, int Q, int kc) {
     double c = 0;
     for (int s = 0; s < B.nside[b]; ++s) {
         int si = B.side_off[b] + s;
         bool coarse = (double)B.side_m[si] / (double)B.l[b] <= k->threshold;
-        int ncand = coarse ? P_lp - 1 : P_hp - 1;
-        if (k->enable_refinement && !coarse) {
-            int x = peel_tile(k->hp_step);
-            ncand = 360 / x + (int)std::lround(x / k->hp_step);
-        }
+        int ncand = coarse ? st.P_lp - 1 : st.P_hp - 1;
+        if (st.tile && !coarse) ncand = 360 / st.tile + (int)std::lround(st.tile / k->hp_step);
         int chunks = (ncand + kc - 1) / kc;
         int nslot = (B.side_nmov[si] + Q - 1) / Q;
         c += (double)nslot * (chunks * (kc * 15.0 + 25.0) + B.side_nfixB[si] * 7.0) + 40.0 * B.l[b] / Q;
@@ -1031,12 +1045,13 @@ int build_plan(dock_ctx* ctx, const BatchH& B, const int32_t* pids, int np, cons
     std::vector<int2> tasks;
     std::vector<double> cost;
     pl->task_off.assign(pl->npairs + 1, 0);
+    const Steps st = steps_of(k);
     for (int pk = 0; pk < np; ++pk)
         for (int b = 0; b < B.n; ++b) {
             const int lq = lanes_log2(t, pl->slice, B.l[b]);
             const int G = 32 >> lq;
             const int ngroup = (N + G - 1) / G;
-            double c = task_cost(B, b, k, 1 << lq, pl->kc);
+            double c = task_cost(B, b, k, st, 1 << lq, pl->kc);
             for (int g = 0; g < ngroup; ++g) {
                 tasks.push_back(make_int2(pk * B.n + b, g | (lq << 16)));
                 cost.push_back(c);
@@ -1193,17 +1208,15 @@ int check_run_args(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, con
 struct LigWork {
     uint64_t cand = 0, upd = 0, bounds = 0, pairs = 0;
 };
-LigWork lig_work(const BatchH& B, int b, const dock_knobs* k) {
-    const int P_hp = n_angles(k->hp_step), P_lp = n_angles(k->lp_step);
+LigWork lig_work(const BatchH& B, int b, const dock_knobs* k, const Steps& st) {
     LigWork w;
     for (int s = 0; s < B.nside[b]; ++s) {
         const int si = B.side_off[b] + s;
         const bool coarse = (double)B.side_m[si] / (double)B.l[b] <= k->threshold;
-        int phases[2] = {coarse ? P_lp - 1 : P_hp - 1, 0};
-        if (k->enable_refinement && !coarse) {
-            const int x = peel_tile(k->hp_step);
-            phases[0] = 360 / x;
-            phases[1] = (int)std::lround(x / k->hp_step);
+        int phases[2] = {coarse ? st.P_lp - 1 : st.P_hp - 1, 0};
+        if (st.tile && !coarse) {
+            phases[0] = 360 / st.tile;
+            phases[1] = (int)std::lround(st.tile / k->hp_step);
         }
         for (int nc : phases) {
             w.cand += nc;
@@ -1222,9 +1235,10 @@ void count_work(dock_ctx* ctx, const BatchH& B, int np, const dock_knobs* k, con
     W.upd.assign(B.n, 0);
     W.bounds.assign(B.n, 0);
     W.pairs.assign(B.n, 0);
+    const Steps st = steps_of(k);
     for (int b = 0; b < B.n; ++b) {
         // one repetition of one pose of ligand b
-        const LigWork w = lig_work(B, b, k);
+        const LigWork w = lig_work(B, b, k, st);
         W.cand[b] = w.cand;
         W.upd[b] = w.upd;
         W.bounds[b] = w.bounds;
@@ -1335,8 +1349,9 @@ int finish_chunk(dock_ctx* ctx, DbSlot& S, const dock_ligand_batch* b, int np, c
     tot.lookups_skipped += gated;
     tot.atom_updates -= gated;
     const uint64_t mult = (uint64_t)k->n_poses * k->repetitions;
+    const Steps st = steps_of(k);
     for (int i = 0; i < nc; ++i) {
-        const LigWork w = lig_work(S.B, i, k);
+        const LigWork w = lig_work(S.B, i, k, st);
         for (int pk = 0; pk < np; ++pk) {
             const uint64_t reps = mult - sk[(size_t)pk * nc + i];
             tot.candidates += reps * w.cand;

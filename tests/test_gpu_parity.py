@@ -177,6 +177,17 @@ def test_error_paths(dk):
                                   np.zeros(0, np.int32))
     with pytest.raises(DockError):
         dk.upload_ligands(bad_atoms)
+    # non-finite and huge coordinates are refused before anything reaches the device, by both entry points
+    for v in (np.nan, np.inf, -np.inf, 2e5):
+        x = b.xyz.copy()
+        x[3, 1] = v
+        bad = synth.LigandBatch(b.atom_off, b.bond_off, b.rot_off, x, b.bonds, b.rot)
+        with pytest.raises(DockError) as ei:
+            dk.upload_ligands(bad)
+        assert ei.value.code == DOCK_ERR_INVALID_ARG and "coordinate" in str(ei.value)
+        with pytest.raises(DockError) as ei:
+            dk.run_database(bad, [pid], C.knobs(), chunk=1)
+        assert ei.value.code == DOCK_ERR_INVALID_ARG and "coordinate" in str(ei.value)
 
 
 def test_bench_workload_sampled(dk):
