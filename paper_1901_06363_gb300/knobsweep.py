@@ -252,15 +252,27 @@ def summary(res):
     keep = dict((k, res[k]) for k in ("space", "knobs", "ligands", "poses", "mean_atoms", "mean_rot", "npts",
                                       "baseline", "baseline_seconds", "pareto", "selection") if k in res)
     keep["fit"] = res.get("fit")
-    keep["table"] = [{k: (round(v, 6) if isinstance(v, float) else v) for k, v in r.items()} for r in res["table"]]
+    cols = list(res["table"][0].keys()) if res["table"] else []
+    sig = lambda v: float(f"{v:.5g}") if isinstance(v, float) else v  # noqa: E731
+    keep["columns"] = cols
+    keep["table"] = [[sig(r[c]) for c in cols] for r in res["table"]]
     if res["space"] == "full":
         # the baseline with tile peeling switched on and nothing else changed
         names = res["knobs"]
         b = dict(zip(names, res["baseline"]))
         pt = [r for r in res["table"] if all(r[nm] == (1 if nm == "enable_refinement" else b[nm]) for nm in names)]
+        pt = [dict(r, speedup=float(f"{r['speedup']:.5g}"), degradation_pct=float(f"{r['degradation_pct']:.5g}"))
+              for r in pt]
         if pt:
             keep["peeling_only"] = dict(speedup=pt[0]["speedup"], degradation_pct=pt[0]["degradation_pct"])
     return keep
+
+
+def dumps_record(s):
+    """The summary as JSON with one table row per line."""
+    head = ",\n".join(f" {json.dumps(k)}: {json.dumps(v)}" for k, v in s.items() if k != "table")
+    rows = ",\n  ".join(json.dumps(r) for r in s.get("table", []))
+    return "{\n" + head + ',\n "table": [\n  ' + rows + "\n ]\n}\n"
 
 
 def main():
@@ -290,8 +302,7 @@ def main():
         s["wall_s"] = round(res["wall_s"], 1)
         s["command"] = "python -m paper_1901_06363_gb300.knobsweep " + " ".join(sys.argv[1:])
         with open(args.summary, "w") as f:
-            json.dump(s, f, indent=1)
-            f.write("\n")
+            f.write(dumps_record(s))
     print(txt)
 
 
