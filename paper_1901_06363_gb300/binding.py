@@ -12,7 +12,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-library_path = os.path.join(HERE, "libgeodock.so")
+# GEODOCK_CHECKED=1 selects the checked build (index checks in every kernel, reported as call errors)
+library_path = os.path.join(HERE, "libgeodock_checked.so" if os.environ.get("GEODOCK_CHECKED") == "1"
+                            else "libgeodock.so")
 
 DOCK_OK = 0
 DOCK_ERR_INVALID_ARG = -1

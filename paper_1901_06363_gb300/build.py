@@ -1,5 +1,9 @@
 """Build libgeodock.so in-tree: every .cu under csrc/ compiled for sm_103a in parallel, then linked.
 
+Also builds libgeodock_checked.so, the same library compiled with GEODOCK_CHECKED: its kernels test the
+indices they derive from their inputs and report the first failure as an error of the call instead of
+touching memory out of bounds (the binding loads it when GEODOCK_CHECKED=1 is set).
+
 Usage: python -m paper_1901_06363_gb300.build [--verbose-ptxas]
 """
 from __future__ import annotations
@@ -14,6 +18,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libgeodock.so")
+OUT_CHECKED = os.path.join(HERE, "libgeodock_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off"]
 
@@ -52,9 +57,9 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(OUT):
+    if not (os.path.exists(OUT) and os.path.exists(OUT_CHECKED)):
         return False
-    t = os.path.getmtime(OUT)
+    t = min(os.path.getmtime(OUT), os.path.getmtime(OUT_CHECKED))
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
@@ -64,12 +69,14 @@ def build(force: bool = False, ptxas_verbose: bool = False, jobs: int | None = N
     cc = nvcc()
     objdir = os.path.join(HERE, "_build")
     os.makedirs(objdir, exist_ok=True)
-    units = _units()
+    # every unit twice: the library and its checked build
+    units = [(src, name, flags, "") for src, name, flags in _units()] + \
+            [(src, name, flags + ["-DGEODOCK_CHECKED"], "checked_") for src, name, flags in _units()]
     extra = ["-Xptxas", "-v"] if ptxas_verbose else []
 
     def compile_one(unit):
-        src, name, flags = unit
-        obj = os.path.join(objdir, name)
+        src, name, flags, pre = unit
+        obj = os.path.join(objdir, pre + name)
         cmd = [cc, *ARCH, *FLAGS, *flags, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -80,14 +87,17 @@ def build(force: bool = False, ptxas_verbose: bool = False, jobs: int | None = N
     with cf.ThreadPoolExecutor(jobs) as ex:
         results = list(ex.map(compile_one, units))
     if ptxas_verbose:
-        for _, log in results:
-            sys.stderr.write(log)
-    tmp = OUT + f".{os.getpid()}.tmp"
-    cmd = [cc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *[o for o, _ in results], "-cudart", "static"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, OUT)
+        for (_, _, _, pre), (_, log) in zip(units, results):
+            if not pre:
+                sys.stderr.write(log)
+    for out, pre in ((OUT, ""), (OUT_CHECKED, "checked_")):
+        objs = [o for (_, _, _, p), (o, _) in zip(units, results) if p == pre]
+        tmp = out + f".{os.getpid()}.tmp"
+        cmd = [cc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs, "-cudart", "static"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, out)
     return OUT
 
 

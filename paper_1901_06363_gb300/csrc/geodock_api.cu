@@ -73,6 +73,7 @@ struct PocketH {
 struct BatchH {
     bool live = false;
     int n = 0, natoms = 0, lmax = 1, nside_total = 0;
+    int nidx = 0, ntor = 0, nchk = 0;  // sizes of the atom-index pool, torsion list and bump-pair rows
     std::vector<int> l, nside;            // per ligand
     std::vector<int> side_m, side_nmov, side_nfixB;  // per side
     std::vector<int> side_off;
@@ -172,6 +173,7 @@ struct dock_ctx {
     dock_tile tile{0, 0, 0};           // forced shape (0 = automatic)
     std::map<std::string, dock_tile> tuned;  // autotuned shapes per (batch, knobs)
     DevBuf counter, pose_key, pose_xyz, res, xyz_res;
+    DevBuf check;  // checked builds: status word of the kernels' index checks
     DevBuf ref_xyz_in, ref_xyz_out, ref_res;                 // host-memory form of dock_refine
     void* stage = nullptr;                                   // pinned staging of ligand uploads
     size_t stage_bytes = 0;
@@ -211,6 +213,41 @@ int fail(dock_ctx* c, int code, const char* fmt, ...) {
             return fail(ctx, e_ == cudaErrorMemoryAllocation ? DOCK_ERR_OUT_OF_MEMORY : DOCK_ERR_CUDA,     \
                         "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);              \
     } while (0)
+
+// Checked builds (GEODOCK_CHECKED): the device status word of the kernels' index checks, allocated on
+// first use; other builds have none (NULL).
+unsigned long long* check_word(dock_ctx* ctx) {
+#ifdef GEODOCK_CHECKED
+    if (!ctx->check.p && ctx->check.ensure(sizeof(unsigned long long)) == cudaSuccess)
+        cudaMemset(ctx->check.p, 0, sizeof(unsigned long long));
+    return ctx->check.as<unsigned long long>();
+#else
+    (void)ctx;
+    return nullptr;
+#endif
+}
+
+// Checked builds: wait for the work on stream s, read and clear the status word, and report a failed check
+// as DOCK_ERR_CUDA with its code and index. Other builds return DOCK_OK at once.
+int read_check(dock_ctx* ctx, cudaStream_t s, unsigned long long* word = nullptr) {
+#ifdef GEODOCK_CHECKED
+    unsigned long long* w = word ? word : check_word(ctx);
+    if (!w) return fail(ctx, DOCK_ERR_OUT_OF_MEMORY, "checked build: no status word");
+    unsigned long long v = 0;
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMemcpy(&v, w, sizeof v, cudaMemcpyDeviceToHost));
+    if (v) {
+        CK(cudaMemset(w, 0, sizeof v));
+        return fail(ctx, DOCK_ERR_CUDA, "index check %u failed at index %u (checked build)", (unsigned)(v >> 32),
+                    (unsigned)(v & 0xffffffffu));
+    }
+#else
+    (void)ctx;
+    (void)s;
+    (void)word;
+#endif
+    return DOCK_OK;
+}
 
 int n_angles(double step) {
     int P = (int)std::ceil(360.0 / step);
@@ -791,6 +828,9 @@ int prep_batch(dock_ctx* ctx, const dock_ligand_batch* b, BatchH& B, BatchImage&
     }
     B.natoms = n > 0 ? b->atom_off[n] : 0;
     B.nside_total = (int)sides.size();
+    B.nidx = (int)idx.size();
+    B.ntor = (int)rtor.size();
+    B.nchk = (int)check.size();
     // one device allocation, 256-byte aligned parts
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     im.xyz = b->xyz;
@@ -1076,6 +1116,9 @@ int build_plan(dock_ctx* ctx, const BatchH& B, const int32_t* pids, int np, cons
     P.pockets = pl->pockets->as<PocketDev>();
     P.tasks = pl->tasks->as<int2>();
     P.ntask = pl->ntask;
+    P.npockets = np;
+    P.nidx = B.nidx;
+    P.check = check_word(ctx);
     P.nlig = B.n;
     P.natoms = B.natoms;
     P.counter = ctx->counter.as<unsigned>();
@@ -1142,6 +1185,7 @@ int build_plan(dock_ctx* ctx, const BatchH& B, const int32_t* pids, int np, cons
 // Enqueue one batched run: reset the queue, persistent sweep, finalize.
 int enqueue_batched(dock_ctx* ctx, Plan* pl, const dock_knobs* k, cudaStream_t s) {
     CK(cudaMemsetAsync(ctx->counter.p, 0, sizeof(unsigned), s));
+    if (pl->P.check) CK(cudaMemsetAsync(pl->P.check, 0, sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(pl->skipped->p, 0, (size_t)std::max(1, pl->npairs) * sizeof(unsigned), s));
     CK(cudaMemsetAsync(pl->looked->p, 0, sizeof(unsigned long long), s));
     // external event records become event nodes when this is captured into a graph; outside a
@@ -1162,6 +1206,7 @@ int enqueue_batched(dock_ctx* ctx, Plan* pl, const dock_knobs* k, cudaStream_t s
 // Plain comparison form: per (pocket, ligand) pair, its own queue reset,
 // sweep launch over that pair's pose groups, and finalize launch.
 int enqueue_plain(dock_ctx* ctx, Plan* pl, const dock_knobs* k, cudaStream_t s) {
+    if (pl->P.check) CK(cudaMemsetAsync(pl->P.check, 0, sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(pl->skipped->p, 0, (size_t)std::max(1, pl->npairs) * sizeof(unsigned), s));
     CK(cudaMemsetAsync(pl->looked->p, 0, sizeof(unsigned long long), s));
     CK(cudaEventRecord(ctx->ev0, s));
@@ -1321,7 +1366,7 @@ int dock_run(dock_ctx* ctx, int batch_id, const int32_t* pocket_ids, int npocket
     if (xyz_out && xbytes) CK(cudaMemcpyAsync(xyz_out, ctx->xyz_res.p, xbytes, kind, s));
     if (!out_on_device) CK(cudaStreamSynchronize(s));
     count_work(ctx, B, npockets, k, pl, launches);
-    return DOCK_OK;
+    return read_check(ctx, s);
 }
 
 }  // extern "C"
@@ -1514,7 +1559,7 @@ int dock_run_database(dock_ctx* ctx, const dock_ligand_batch* b, const int32_t* 
     tot.kernel_launches = launches;
     tot.sweep_ms = -1.0;
     ctx->stats = tot;
-    return DOCK_OK;
+    return read_check(ctx, s);
 }
 
 int dock_run_trace(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs* k, const dock_trace* tr,
@@ -1544,6 +1589,7 @@ int dock_run_trace(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs*
     P.tr.init_xyz = tr->init_xyz;
     P.tr.pose_xyz = tr->pose_xyz;
     CK(cudaMemsetAsync(ctx->counter.p, 0, sizeof(unsigned), s));
+    if (P.check) CK(cudaMemsetAsync(P.check, 0, sizeof(unsigned long long), s));
     if (pl->ntask > 0) CK(launch_sweep(pl->kc, P, k->score_mode, k->clip_box, pl->grid, pl->block, pl->smem, s));
     if (pl->npairs > 0) {
         finalize_kernel<<<(pl->npairs + 3) / 4, 128, 0, s>>>(pl->F);
@@ -1552,7 +1598,7 @@ int dock_run_trace(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs*
     if (out && pl->npairs)
         CK(cudaMemcpyAsync(out, ctx->res.p, (size_t)pl->npairs * sizeof(dock_result), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    return DOCK_OK;
+    return read_check(ctx, s);
 }
 
 int dock_autotune(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs* k, dock_tile* best, void* stream) {
@@ -1630,6 +1676,7 @@ constexpr int kStaticAngles = 361;                       // angles per table (1 
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t kOffCounter = 0;
+constexpr size_t kOffCheck = 8;  // status word of the index checks (checked builds)
 constexpr size_t kOffTables = 256;
 constexpr size_t kOffTasks = kOffTables + align256(3 * kStaticAngles * sizeof(float2));
 constexpr size_t kOffKeys = kOffTasks + align256(kStaticPoseSlots * sizeof(int2));
@@ -1672,10 +1719,14 @@ struct StaticTables {
 // batched form chooses them (the smallest power of two >= lq0 whose pose
 // group of 32 >> lq poses fits the warp's coordinate slice). Every ligand
 // gets ngroup slots; a group past its ligand's poses is an idle task.
-__global__ void static_setup_kernel(const __grid_constant__ StaticTables tabs, unsigned* counter, float2* tab_out,
-                                    int2* tasks, const LigDev* lig, int nlig, int ngroup, int lq0, int slice) {
+__global__ void static_setup_kernel(const __grid_constant__ StaticTables tabs, unsigned* counter,
+                                    unsigned long long* check, float2* tab_out, int2* tasks, const LigDev* lig,
+                                    int nlig, int ngroup, int lq0, int slice) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t == 0) *counter = 0u;
+    if (t == 0) {
+        *counter = 0u;
+        *check = 0ull;
+    }
     if (t < 3 * kStaticAngles) tab_out[t] = tabs.t[t / kStaticAngles][t % kStaticAngles];
     if (t < (int64_t)nlig * ngroup) {
         const int b = (int)(t / ngroup), g = (int)(t % ngroup);
@@ -1755,8 +1806,8 @@ extern "C" int dock_run_static(dock_ctx* ctx, int batch_id, int pocket_id, const
     float2* tab = reinterpret_cast<float2*>(base + kOffTables);
     const int64_t nset = std::max<int64_t>(3 * kStaticAngles, ntask);
     static_setup_kernel<<<(unsigned)((nset + 255) / 256), 256, 0, s>>>(
-        tabs, reinterpret_cast<unsigned*>(base + kOffCounter), tab, reinterpret_cast<int2*>(base + kOffTasks), B.d_lig,
-        B.n, ngroup, lq0, slice);
+        tabs, reinterpret_cast<unsigned*>(base + kOffCounter), reinterpret_cast<unsigned long long*>(base + kOffCheck),
+        tab, reinterpret_cast<int2*>(base + kOffTasks), B.d_lig, B.n, ngroup, lq0, slice);
     CK(cudaGetLastError());
 
     const PocketDev* pdev = ctx->pockets[pocket_id].dev->as<PocketDev>();
@@ -1768,6 +1819,11 @@ extern "C" int dock_run_static(dock_ctx* ctx, int batch_id, int pocket_id, const
     P.pockets = pdev;
     P.tasks = reinterpret_cast<const int2*>(base + kOffTasks);
     P.ntask = ntask;
+    P.npockets = 1;
+    P.nidx = B.nidx;
+#ifdef GEODOCK_CHECKED
+    P.check = reinterpret_cast<unsigned long long*>(base + kOffCheck);
+#endif
     P.nlig = B.n;
     P.natoms = B.natoms;
     P.counter = reinterpret_cast<unsigned*>(base + kOffCounter);
@@ -1814,7 +1870,8 @@ extern "C" int dock_run_static(dock_ctx* ctx, int batch_id, int pocket_id, const
         finalize_kernel<<<(B.n + 3) / 4, 128, 0, s>>>(F);
         CK(cudaGetLastError());
     }
-    return DOCK_OK;
+    // checked builds wait here and report a failed index check
+    return read_check(ctx, s, P.check);
 }
 
 // ------------------------------------------------------------ local refinement
@@ -1834,9 +1891,21 @@ int check_pocket(dock_ctx* ctx, int pocket_id) {
     return DOCK_OK;
 }
 
+BatchBounds bounds_of(dock_ctx* ctx, const BatchH& B) {
+    BatchBounds bb{};
+    bb.natoms = B.natoms;
+    bb.nside = B.nside_total;
+    bb.nidx = B.nidx;
+    bb.ntor = B.ntor;
+    bb.nchk = B.nchk;
+    bb.lmax = B.lmax;
+    bb.check = check_word(ctx);
+    return bb;
+}
+
 ScoreParams score_params(dock_ctx* ctx, const BatchH& B, const PocketDev* pocket_dev) {
-    (void)ctx;
     ScoreParams P{};
+    P.bounds = bounds_of(ctx, B);
     P.lig = B.d_lig;
     P.side = B.d_side;
     P.idx = B.d_idx;
@@ -1911,6 +1980,7 @@ int refine_impl(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const 
     P.xyz_in = xin;
     P.xyz_out = xout;
     P.result = res;
+    P.bounds = bounds_of(ctx, B);
     std::vector<DevBuf> tbuf(10);
     const int ns = npairs * k->refine_steps;
     if (tr) {
@@ -1934,6 +2004,7 @@ int refine_impl(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const 
         P.tr.status = tbuf[8].as<int32_t>();
     }
     CK(launch_refine(P, B.lmax, B.tmax, s));
+    if ((rc = read_check(ctx, s))) return rc;
     if (tr) {
         CK(cudaStreamSynchronize(s));
         CK(cudaMemcpy(tr->G, P.tr.G, (size_t)ns * tr->gstride * 4, cudaMemcpyDeviceToHost));
@@ -1984,7 +2055,7 @@ int dock_score_trilinear(dock_ctx* ctx, int batch_id, int pocket_id, int clip, c
     P.x = xyz;
     P.out = o;
     CK(launch_score(P, B.lmax, SCORE_FWD, s));
-    return DOCK_OK;
+    return read_check(ctx, s);
 }
 
 int dock_score_trilinear_grad(dock_ctx* ctx, int batch_id, int pocket_id, int clip, const float* xyz,
@@ -2003,7 +2074,7 @@ int dock_score_trilinear_grad(dock_ctx* ctx, int batch_id, int pocket_id, int cl
     P.grad_in = grad_o;
     P.out = grad_xyz;
     CK(launch_score(P, B.lmax, SCORE_BWD, s));
-    return DOCK_OK;
+    return read_check(ctx, s);
 }
 
 int dock_dof_apply(dock_ctx* ctx, int batch_id, const float* x, const float* q, int qstride, float* z, void* stream) {
@@ -2019,7 +2090,7 @@ int dock_dof_apply(dock_ctx* ctx, int batch_id, const float* x, const float* q, 
     P.qstride = qstride;
     P.out = z;
     CK(launch_score(P, B.lmax, DOF_APPLY, (cudaStream_t)stream));
-    return DOCK_OK;
+    return read_check(ctx, (cudaStream_t)stream);
 }
 
 int dock_dof_grad(dock_ctx* ctx, int batch_id, const float* x, const float* q, int qstride, const float* grad_z,
@@ -2037,7 +2108,7 @@ int dock_dof_grad(dock_ctx* ctx, int batch_id, const float* x, const float* q, i
     P.grad_in = grad_z;
     P.out = grad_q;
     CK(launch_score(P, B.lmax, DOF_GRAD, (cudaStream_t)stream));
-    return DOCK_OK;
+    return read_check(ctx, (cudaStream_t)stream);
 }
 
 int dock_refine(dock_ctx* ctx, int batch_id, const int32_t* pocket_ids, int npockets, const dock_knobs* k,

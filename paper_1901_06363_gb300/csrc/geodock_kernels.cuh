@@ -95,6 +95,9 @@ struct SweepParams {
     const PocketDev* pockets;
     const int2* tasks;  // (pair, group | log2(lanes per pose) << 16); pair = pocket * nlig + ligand
     int ntask;
+    int npockets;        // pockets of the run (pair = pocket * nlig + ligand)
+    int nidx;            // bytes of the batch's atom-index pool
+    unsigned long long* check;  // checked builds: the first failed index check, (code << 32) | index
     int slice;           // floats of shared memory per warp for its poses' coordinates
     int bw;              // 64-bit bump words per lane (ceil of the largest phase / 64)
     int nlig;
@@ -128,6 +131,25 @@ struct SweepParams {
 };
 
 // ------------------------------------------------------------------ helpers
+
+// Checked builds (GEODOCK_CHECKED): an index that a kernel derives from its
+// inputs is tested before use; a failed test records (code << 32) | index in
+// the run's status word (the first failure wins) and the access is skipped,
+// so the host can report the bad index instead of the GPU faulting. Codes:
+// 1 ligand atoms beyond the batch, 2 a pose group larger than its coordinate
+// slice, 3 index lists beyond the pool or the staging area, 4 an atom index
+// beyond its ligand, 5 a phase with more candidates than bump words, 6 a
+// per-pose output beyond the run, 7 a pocket beyond the run, 8 a torsion or
+// bump-pair row beyond the batch (refinement). Other builds test nothing.
+#ifdef GEODOCK_CHECKED
+__device__ __forceinline__ bool check_ok(unsigned long long* st, bool cond, unsigned code, unsigned long long idx) {
+    if (!cond && st) atomicCAS(st, 0ull, ((unsigned long long)code << 32) | (idx & 0xffffffffull));
+    return cond;
+}
+#define GD_OK(st, cond, code, idx) ::gd::check_ok((st), (cond), (code), (unsigned long long)(idx))
+#else
+#define GD_OK(st, cond, code, idx) true
+#endif
 
 // floor(t) as an unsigned voxel index, for 0 <= t < 2^23: adding 2^23 with
 // round-toward-zero leaves floor(t) in the low mantissa bits. Any t < 0 (or
@@ -319,6 +341,11 @@ __host__ __device__ constexpr int ptab_pad(int kc) { return kc > 12 ? kc : 12; }
 __host__ __device__ constexpr int warp_extra_floats(int kc, int bw) {
     return bw * 64 + 2 * (64 * bw + ptab_pad(kc)) + IDX_FLOATS;
 }
+// every warp's area starts on a 16-byte boundary (the angle table is read as float4): slices are multiples
+// of 4 floats, and so are these parts
+static_assert(IDX_FLOATS % 4 == 0 && (2 * ptab_pad(8)) % 4 == 0 && (2 * ptab_pad(18)) % 4 == 0 &&
+                  (2 * ptab_pad(36)) % 4 == 0,
+              "per-warp shared-memory areas keep 16-byte alignment");
 
 // 32-bit sums over the Q lanes of a pose.
 __device__ __forceinline__ uint32_t group_add_u(uint32_t v, int Q) {
@@ -501,6 +528,14 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
         const int ps = lane >> lq;   // pose slot
         const int q = lane & (Q - 1);
         const int pocket = tk.x / P.nlig, b = tk.x % P.nlig;
+#ifdef GEODOCK_CHECKED
+        if (!GD_OK(P.check, pocket < P.npockets, 7, pocket)) continue;
+        {
+            const LigDev Lc = P.lig[b];
+            if (!GD_OK(P.check, Lc.atom_off >= 0 && Lc.atom_off + Lc.l <= P.natoms, 1, b)) continue;
+            if (!GD_OK(P.check, 3 * Lc.l * G <= P.slice, 2, b)) continue;
+        }
+#endif
         const PocketDev& pd = P.pockets[pocket];
         const uint16_t* __restrict__ K = pd.K;
         const LigDev L = P.lig[b];
@@ -584,8 +619,21 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                     const bool peel = P.peel && !coarse;
                     // the sweep's index lists, staged in shared memory: M\{c}, then F\{b}, b, c
                     __syncwarp();
+#ifdef GEODOCK_CHECKED
+                    const bool lists_ok =
+                        GD_OK(P.check, sd.nmov + sd.nfixS <= 4 * (IDX_FLOATS - 1), 3, L.side_off + si) &&
+                        GD_OK(P.check, sd.mov_off >= 0 && sd.mov_off + sd.nmov <= P.nidx, 3, L.side_off + si) &&
+                        GD_OK(P.check, sd.fix_off >= 0 && sd.fix_off + sd.nfixS <= P.nidx, 3, L.side_off + si) &&
+                        GD_OK(P.check, sd.c < L.l && sd.b < L.l, 4, L.side_off + si);
+                    if (!lists_ok) continue;  // the sweep is skipped (warp-uniform: one descriptor per warp)
+                    for (int i = lane; i < sd.nmov + sd.nfixS; i += 32) {
+                        const uint8_t a = P.idx[i < sd.nmov ? sd.mov_off + i : sd.fix_off + (i - sd.nmov)];
+                        sidx[i] = GD_OK(P.check, a < L.l, 4, L.side_off + si) ? a : 0;
+                    }
+#else
                     for (int i = lane; i < sd.nmov + sd.nfixS; i += 32)
                         sidx[i] = P.idx[i < sd.nmov ? sd.mov_off + i : sd.fix_off + (i - sd.nmov)];
+#endif
                     __syncwarp();
                     const uint8_t* mov = sidx;
                     const uint8_t* fix = sidx + sd.nmov;
@@ -663,6 +711,9 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                         // to the circle of moving atom x is sqrt((rho_y - r_x)^2 + (h_y - h_x)^2)
                         // (rho: distance from the axis, h: position along it); pairs that come within
                         // the threshold get the arc of angles where they do marked.
+#ifdef GEODOCK_CHECKED
+                        if (!GD_OK(P.check, ncand <= 64 * P.bw, 5, ncand)) ncand = 64 * P.bw;
+#endif
                         const int nw = (ncand + 63) >> 6;
                         for (int w = 0; w < nw; ++w) col[w * 32] = 0ull;
                         // the phase's angles, the same for every lane; (1, 0) past the end
@@ -901,7 +952,8 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
         }
         if (P.lookups_skipped && lane == 0 && *wlook) atomicAdd(P.lookups_skipped, (unsigned long long)*wlook);
         // ---- per-pose result
-        if (active && q == 0) {
+        if (active && q == 0 &&
+            GD_OK(P.check, (int64_t)tk.x < (int64_t)P.npockets * P.nlig && p < P.n_poses, 6, tk.x)) {
             const int64_t pi = (int64_t)tk.x * P.n_poses + p;
             P.pose_key[pi] = live ? make_key(S_inc, p) : ~0ull;
             float* o = P.pose_xyz + ((int64_t)pocket * P.natoms * P.n_poses + (int64_t)L.atom_off * P.n_poses +

@@ -24,6 +24,9 @@ __global__ void __launch_bounds__(128) refine_kernel(RefineParams P, int lmax, i
     const int pocket = pair / P.nlig, b = pair % P.nlig;
     const LigDev L = P.lig[b];
     const RefLigDev R = P.rlig[b];
+#ifdef GEODOCK_CHECKED
+    if (!ligand_ok(P.bounds, L, R, P.side, P.idx, P.rtor, b)) return;
+#endif
     const PocketDev& pd = P.pockets[pocket];
     const Frame F = frame_of(pd);
     const int l = L.l;
@@ -149,6 +152,9 @@ __global__ void __launch_bounds__(128) score_fwd_kernel(ScoreParams P, int lmax)
     if (b >= P.nlig) return;
     float* z = rsm + (size_t)warp * 3 * lmax;
     const LigDev L = P.lig[b];
+#ifdef GEODOCK_CHECKED
+    if (!ligand_ok(P.bounds, L, P.rlig[b], P.side, P.idx, P.rtor, b)) return;
+#endif
     const PocketDev& pd = *P.pocket;
     for (int e = lane; e < 3 * L.l; e += 32) z[e] = P.x[(int64_t)L.atom_off * 3 + e];
     __syncwarp();
@@ -166,6 +172,9 @@ __global__ void __launch_bounds__(128) score_bwd_kernel(ScoreParams P, int lmax)
     float* z = rsm + (size_t)warp * 6 * lmax;
     float* dS = z + 3 * lmax;
     const LigDev L = P.lig[b];
+#ifdef GEODOCK_CHECKED
+    if (!ligand_ok(P.bounds, L, P.rlig[b], P.side, P.idx, P.rtor, b)) return;
+#endif
     const PocketDev& pd = *P.pocket;
     const Frame F = frame_of(pd);
     for (int e = lane; e < 3 * L.l; e += 32) z[e] = P.x[(int64_t)L.atom_off * 3 + e];
@@ -198,6 +207,9 @@ __global__ void __launch_bounds__(128) dof_apply_kernel(ScoreParams P, int lmax)
     float* y = rsm + (size_t)warp * 3 * lmax;
     const LigDev L = P.lig[b];
     const RefLigDev R = P.rlig[b];
+#ifdef GEODOCK_CHECKED
+    if (!ligand_ok(P.bounds, L, R, P.side, P.idx, P.rtor, b)) return;
+#endif
     apply_dofs(P, L, R, b, y);
     for (int e = lane; e < 3 * L.l; e += 32) P.out[(int64_t)L.atom_off * 3 + e] = y[e];
 }
@@ -212,6 +224,9 @@ __global__ void __launch_bounds__(128) dof_grad_kernel(ScoreParams P, int lmax) 
     float* p = y + 3 * lmax;
     const LigDev L = P.lig[b];
     const RefLigDev R = P.rlig[b];
+#ifdef GEODOCK_CHECKED
+    if (!ligand_ok(P.bounds, L, R, P.side, P.idx, P.rtor, b)) return;
+#endif
     const float3 g = apply_dofs(P, L, R, b, y);
     for (int e = lane; e < 3 * L.l; e += 32) p[e] = P.grad_in[(int64_t)L.atom_off * 3 + e];
     __syncwarp();

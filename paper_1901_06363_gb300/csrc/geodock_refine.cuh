@@ -49,6 +49,12 @@ struct RefLigDev {
 // accepted step (at most LAMBDA_MAX) and shrinks by SHRINK after a rejected one.
 constexpr float REFINE_LAMBDA0 = 0.25f, REFINE_LAMBDA_MAX = 1.0f, REFINE_GROW = 1.5f, REFINE_SHRINK = 0.5f;
 
+// Sizes of a batch's arrays, for the index checks of checked builds (GEODOCK_CHECKED; see GD_OK).
+struct BatchBounds {
+    int natoms, nside, nidx, ntor, nchk, lmax;
+    unsigned long long* check;  // status word of the checks (nullable)
+};
+
 struct RefineTraceDev {
     int gstride;        // 6 + largest T
     float* G;           // [pair][step][gstride]
@@ -78,6 +84,7 @@ struct RefineParams {
     float* result;        // dock_result words per pair: score, pose (-1), status, reserved
     int trace_on;
     RefineTraceDev tr;
+    BatchBounds bounds;
 };
 
 // Differentiable-score launches: one warp per ligand of a batch.
@@ -93,6 +100,7 @@ struct ScoreParams {
     const float* q;       // [ligand][qstride]
     const float* grad_in; // score backward: d L / d o per ligand (nullable: ones); dof backward: d L / d z
     float* out;           // o per ligand / z / grad
+    BatchBounds bounds;
 };
 
 // ----------------------------------------------------------------- helpers
@@ -329,5 +337,32 @@ __device__ __forceinline__ void warp_dof_grad(const SideDev* side, const uint8_t
         if (lane == 0) put(6 + rt.k, dot3(k, s));
     }
 }
+
+#ifdef GEODOCK_CHECKED
+// Checked builds: every array a warp of these kernels reads for ligand b lies inside the batch, and every atom
+// index it reads lies inside the ligand (codes 1, 2, 3, 4, 8 of GD_OK). Lane 0 checks, the warp agrees.
+static __device__ __noinline__ bool ligand_ok(const BatchBounds& B, const LigDev& L, const RefLigDev& R, const SideDev* side,
+                                       const uint8_t* idx, const RefTorDev* rtor, int b) {
+    bool ok = true;
+    if ((threadIdx.x & 31) == 0) {
+        unsigned long long* st = B.check;
+        ok = GD_OK(st, L.l >= 1 && L.atom_off >= 0 && L.atom_off + L.l <= B.natoms, 1, b) &&
+             GD_OK(st, L.l <= B.lmax, 2, b) &&
+             GD_OK(st, L.side_off >= 0 && L.side_off + L.nside <= B.nside, 3, b) &&
+             GD_OK(st, R.tor_off >= 0 && R.tor_off + R.T <= B.ntor, 8, b) &&
+             GD_OK(st, R.check_off >= 0 && R.check_off + L.l * R.wpr <= B.nchk && R.wpr * 32 >= L.l, 8, b);
+        for (int e = 0; ok && e < R.T; ++e) {
+            const RefTorDev rt = rtor[R.tor_off + e];
+            ok = GD_OK(st, rt.side >= 0 && rt.side < L.nside && rt.k >= 0 && rt.k < R.T, 8, b);
+            if (!ok) break;
+            const SideDev sd = side[L.side_off + rt.side];
+            ok = GD_OK(st, sd.mov_off >= 0 && sd.mov_off + sd.nmov <= B.nidx, 3, b) &&
+                 GD_OK(st, sd.c < L.l && sd.b < L.l, 4, b);
+            for (int j = 0; ok && j < sd.nmov; ++j) ok = GD_OK(st, idx[sd.mov_off + j] < L.l, 4, b);
+        }
+    }
+    return __shfl_sync(FULL, ok ? 1 : 0, 0) != 0;
+}
+#endif
 
 }  // namespace gd
