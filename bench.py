@@ -5,11 +5,18 @@ Workload: 1,024 synthetic ligands (16-64 atoms, 2-12 rotatable bonds) x one
 threshold 2.0 Å, nearest-voxel score, FP32. A step docks the whole batch
 (every (ligand, pose) through the full greedy sweep, best pose per ligand).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--scaling weak|strong]
 
 Prints one JSON line. Under torchrun each rank docks its own 1,024 ligands
 (weak scaling, no collective on the data path); rank 0 prints the line.
---impl reference times the FP64 CPU oracle (the reference arm) on the host.
+--scaling strong splits the one workload over the ranks (LPT on the work
+model) and gathers its results. --impl reference times the FP64 CPU oracle
+(the reference arm) on the host. Besides the headline workload the line
+carries the other workloads (single ligand, a knob-sweep point,
+differentiation, multi-pocket), each batched against the plain form, the
+roofline of the sweep kernel by its algorithmic work
+(FP32 operations, field gathers of feasible candidates, HBM bytes), and the
+oracle on bounded samples of each workload (16 host cores and one).
 """
 from __future__ import annotations
 
@@ -398,6 +405,69 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_strong(args):
+    """Strong scaling: the one 1,024-ligand workload split over the ranks by the LPT work model (shard.py);
+    each rank docks its shard, the results are gathered to rank 0 once after the timed steps and checked to
+    cover every ligand once. Prints the timed throughput of the whole workload."""
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1901_06363_gb300 import Docker, shard
+    pk, batch, kn = workload(0)
+    costs = shard.ligand_costs(batch, 36, kn["n_poses"], kn["repetitions"])
+    idx = shard.lpt_shards(costs, world)[rank]
+    sub = batch.subset(idx)
+    dk = Docker(local)
+    pid = dk.init_pocket(pk)
+    bid = dk.upload_ligands(sub, ids=idx + batch.id_base)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    n, natoms = sub.n, int(sub.atom_off[-1])
+    out = torch.zeros(max(n, 1) * 4, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        dk.run(bid, [pid], kn, n, natoms, out=out, xyz_out=None, stream=stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            dk.run(bid, [pid], kn, n, natoms, out=out, xyz_out=None, stream=stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    total_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    if dist:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    from paper_1901_06363_gb300 import RESULT_DTYPE
+    local_res = out[:n * 4].cpu().numpy().view(RESULT_DTYPE)
+    res = shard.gather_results(idx, local_res, batch.n) if dist else local_res
+    if rank == 0:
+        line = {"metric": METRIC, "value": batch.n * args.steps / total_s, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "parallelism": f"ligand shards over {world} rank(s), LPT on the "
+                           "work model", "shard_sizes": [int(len(p)) for p in shard.lpt_shards(costs, world)],
+                           "l2": "flushed between timed steps (256 MiB write)"},
+                "all_ligands_docked": bool(len(res) == batch.n and np.all(res["status"] == 0)),
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    dk.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 def run_ours(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -616,11 +686,16 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--scaling", choices=["weak", "strong"], default="weak",
+                    help="weak: every rank docks its own 1,024 ligands; strong: the ranks split one 1,024-ligand "
+                         "workload (LPT) and gather its results")
     ap.add_argument("--no-baselines", action="store_true",
                     help="skip the CPU oracle, end-to-end and plain-form legs (for profiling the timed steps)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.scaling == "strong":
+        run_strong(args)
     else:
         run_ours(args)
 
