@@ -38,3 +38,29 @@ def test_traffic_key_ignores_comments_only():
     assert m.kernel_code_sha(text) == base
     assert m.kernel_code_sha("// a new comment\n" + text.replace("// ", "//  ", 3) + "\n/* x */\n\n") == base
     assert m.kernel_code_sha(text.replace("constexpr int IDX_FLOATS = 68;", "constexpr int IDX_FLOATS = 72;")) != base
+
+
+def test_sweep_moving_atoms_follow_the_fragments():
+    import indep
+    m = _bench()
+    l, t = synth.ligand_sizes(6, 9, 0, [12, 40, 0, 6])
+    b = synth.ligand_batch(6, l, t)
+    nm = m.sweep_nmov(b)
+    for i in range(b.n):
+        x, bonds, rot = indep.ligand(b, i)
+        sides = indep.sides(len(x), bonds, rot)
+        assert list(nm[i]) == [int(mv.sum()) - 1 for mv, _, _ in sides]
+
+
+def test_roofline_takes_the_slowest_resource():
+    m = _bench()
+    st = dict(atom_updates=600, lookups_skipped=400, bump_pairs=1000, candidates=100)
+    fw = dict(feasible_lookups=300)
+    rates = dict(fma_per_s=1e4, tex_local_per_s=100.0)
+    bound, res = m.roofline_8d(st, fw, 10.0, rates, traffic=5000, hbm_gbs=1e-6)
+    # fp32: 7 * 1000 + 3 * 1000 + 100 = 10100 lane-ops at 1e4/s = 1.01 s; texture 300 / 100 = 3 s; hbm 5 s
+    assert res["fp32"]["work"] == 10100 and abs(res["fp32"]["time_s"] - 1.01) < 1e-12
+    assert res["texture"]["time_s"] == 3.0 and abs(res["hbm"]["time_s"] - 5.0) < 1e-9
+    assert bound == "hbm" and abs(res["hbm"]["frac"] - 0.5) < 1e-9
+    bound, res = m.roofline_8d(st, fw, 10.0, rates, traffic=None, hbm_gbs=1.0)
+    assert bound == "texture" and res["texture"]["frac"] == 0.3
