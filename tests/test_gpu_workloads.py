@@ -81,3 +81,23 @@ def test_knob_sweep_combinations(dk):
         key = (kn["hp_step"], kn["n_poses"], kn["repetitions"])
         _replay_sample(dk, pks[0], pid, b, kn, sample, best[key][sample])
     dk.release_batch(bid)
+
+
+@pytest.mark.parametrize("point", [(2.0, 45.0, 0.3, 2, 1), (5.0, 90.0, 0.8, 1, 1), (1.0, 45.0, 0.6, 3, 1),
+                                   (3.0, 90.0, 0.3, 2, 0)])
+def test_full_design_space_points(dk, point):
+    """Points of the paper's full design space (Sec. 5.2: high-precision step, low-precision step, threshold,
+    repetitions, tile peeling) with a threshold > 0, on 16 of the exploration's lognormal ligands and 8 poses:
+    the launch of 2,000 ligands equals the sampled ligands traced alone, which replay against the oracle."""
+    hp, lp, thr, reps, peel = point
+    pks, _, _ = C.knob_sweep(n=1)
+    b = C.sweep_batch(2000)
+    kn = C.knobs(hp_step=hp, lp_step=lp, threshold=thr, repetitions=reps, enable_refinement=peel, n_poses=8, seed=3)
+    pid = dk.init_pocket(pks[0])
+    bid = dk.upload_ligands(b)
+    res, _ = dk.run(bid, [pid], kn, b.n, int(b.atom_off[-1]), xyz=False)
+    assert (res["status"] == 0).mean() > 0.9
+    sample = np.sort(np.random.default_rng(int(hp * 100 + thr * 10)).choice(b.n, 16, replace=False))
+    st = _replay_sample(dk, pks[0], pid, b, kn, sample, res[sample])
+    assert st["candidates"] > 1000
+    dk.release_batch(bid)
