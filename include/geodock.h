@@ -21,6 +21,11 @@
  *  - A context is thread-compatible, not thread-safe: one thread at a time.
  *  - Per-pair status flags (e.g. "every initial pose was outside the box")
  *    are results, not errors.
+ *  - The same ABI is also built as a checked library (GEODOCK_CHECKED): its
+ *    kernels test every index they derive from their inputs, and a call
+ *    whose kernels found a bad one returns DOCK_ERR_CUDA with the check's
+ *    code and index in dock_last_error() (the call then waits for its work).
+ *    It is a debugging aid; results are otherwise those of the library.
  *
  * Units: coordinates in Å, angles in degrees. Internally the path works in
  * grid units of the pocket (Å / h) in FP32; grid values are exact integers.
