@@ -45,7 +45,7 @@ extern "C" {
 #define DOCK_ERR_OUT_OF_MEMORY (-3) /* a device allocation failed */
 #define DOCK_ERR_CUDA (-4)          /* a CUDA runtime call failed (text in dock_last_error) */
 #define DOCK_ERR_TIMEOUT (-5)       /* a bounded device-side wait gave up */
-#define DOCK_ERR_UNSUPPORTED (-6)   /* a knob combination this build does not run */
+#define DOCK_ERR_UNSUPPORTED (-6)   /* a knob combination the library does not run */
 
 /* largest ligand (atoms) and the largest grid edge (voxels) */
 #define DOCK_MAX_ATOMS 255
