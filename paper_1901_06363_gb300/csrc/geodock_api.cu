@@ -4,6 +4,7 @@
 // angle tables), the persistent batched launch in a CUDA graph, the plain
 // one-launch-per-pair form, and the trace run.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -28,6 +29,15 @@
 using namespace gd;
 
 namespace {
+
+// A named NVTX range over a scope (visible to a profiler's timeline; without one attached the calls do
+// nothing).
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 struct DevBuf {
     void* p = nullptr;
@@ -206,12 +216,17 @@ int fail(dock_ctx* c, int code, const char* fmt, ...) {
     return code;
 }
 
+// A failed runtime call returns its code as DOCK_ERR_OUT_OF_MEMORY or DOCK_ERR_CUDA. The runtime's
+// last-error state is cleared on the way out, so that a failure that leaves the context usable (an
+// allocation that did not fit) is not reported again by the next call's launch checks.
 #define CK(call)                                                                                           \
     do {                                                                                                   \
         cudaError_t e_ = (call);                                                                           \
-        if (e_ != cudaSuccess)                                                                             \
+        if (e_ != cudaSuccess) {                                                                           \
+            (void)cudaGetLastError();                                                                      \
             return fail(ctx, e_ == cudaErrorMemoryAllocation ? DOCK_ERR_OUT_OF_MEMORY : DOCK_ERR_CUDA,     \
                         "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);              \
+        }                                                                                                  \
     } while (0)
 
 // Checked builds (GEODOCK_CHECKED): the device status word of the kernels' index checks, allocated on
@@ -632,6 +647,7 @@ void dock_destroy(dock_ctx* ctx) {
 const char* dock_last_error(const dock_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 
 int dock_init_pocket(dock_ctx* ctx, const dock_pocket* p, int* pocket_id) {
+    Range range("dock_init_pocket");
     if (!ctx || !p || !pocket_id) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_init_pocket: NULL argument");
     CK(cudaSetDevice(ctx->device));
     if (p->nx < 2 || p->ny < 2 || p->nz < 2 || p->nx > DOCK_MAX_GRID || p->ny > DOCK_MAX_GRID || p->nz > DOCK_MAX_GRID)
@@ -883,6 +899,7 @@ int ensure_pinned(dock_ctx* ctx, void** p, size_t* have, size_t want) {
 extern "C" {
 
 int dock_upload_ligands(dock_ctx* ctx, const dock_ligand_batch* b, int* batch_id) {
+    Range range("dock_upload_ligands");
     if (!ctx || !b || !batch_id) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_upload_ligands: NULL argument");
     CK(cudaSetDevice(ctx->device));
     BatchH B;
@@ -1316,6 +1333,7 @@ extern "C" {
 
 int dock_run(dock_ctx* ctx, int batch_id, const int32_t* pocket_ids, int npockets, const dock_knobs* k,
              dock_result* out, float* xyz_out, int out_on_device, void* stream) {
+    Range range("dock_run");
     int rc = check_run_args(ctx, batch_id, pocket_ids, npockets, k);
     if (rc) return rc;
     if (!out) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_run: NULL out");
@@ -1433,6 +1451,7 @@ int dock_measure_peaks(dock_ctx* ctx, int pocket_id, dock_peaks* out, void* stre
 
 int dock_run_database(dock_ctx* ctx, const dock_ligand_batch* b, const int32_t* pocket_ids, int npockets,
                       const dock_knobs* k, int chunk, dock_result* out, float* xyz_out, void* stream) {
+    Range range("dock_run_database");
     if (!ctx) return DOCK_ERR_INVALID_ARG;
     if (!b || !out) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_run_database: NULL argument");
     if (chunk < 1) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_run_database: chunk < 1");
@@ -1515,7 +1534,10 @@ int dock_run_database(dock_ctx* ctx, const dock_ligand_batch* b, const int32_t* 
         v.rot = b->rot ? b->rot + r0 : nullptr;
         v.id_base = b->id_base + S.c0;
         v.ids = b->ids ? b->ids + S.c0 : nullptr;
-        if ((rc = prep_batch(ctx, &v, S.B, S.im))) {
+        nvtxRangePushA("database chunk: host preparation");
+        rc = prep_batch(ctx, &v, S.B, S.im);
+        nvtxRangePop();
+        if (rc) {
             // a bad ligand in chunk c: report it by its index in the database
             ctx->err = "ligands " + std::to_string(S.c0) + ".." + std::to_string(S.c1 - 1) + ": " + ctx->err;
             for (DbSlot& o : ctx->db)
@@ -1564,6 +1586,7 @@ int dock_run_database(dock_ctx* ctx, const dock_ligand_batch* b, const int32_t* 
 
 int dock_run_trace(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs* k, const dock_trace* tr,
                    dock_result* out, void* stream) {
+    Range range("dock_run_trace");
     int rc = check_run_args(ctx, batch_id, &pocket_id, 1, k);
     if (rc) return rc;
     if (!tr || !tr->chosen_k || !tr->cand_S || !tr->cand_status || !tr->pose_S || !tr->pose_init_S ||
@@ -1602,6 +1625,7 @@ int dock_run_trace(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs*
 }
 
 int dock_autotune(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs* k, dock_tile* best, void* stream) {
+    Range range("dock_autotune");
     int32_t pid = pocket_id;
     int rc = check_run_args(ctx, batch_id, &pid, 1, k);
     if (rc) return rc;
@@ -1942,6 +1966,7 @@ int pocket_set(dock_ctx* ctx, const int32_t* pids, int np, const PocketDev** out
 
 int refine_impl(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const dock_knobs* k, const float* xyz_in,
                 dock_result* out, float* xyz_out, int on_device, const dock_refine_trace_buf* tr, cudaStream_t s) {
+    Range range("dock_refine");
     int rc = check_run_args(ctx, batch_id, pids, np, k);
     if (rc) return rc;
     if (!xyz_in || !out || !xyz_out) return fail(ctx, DOCK_ERR_INVALID_ARG, "dock_refine: NULL buffer");

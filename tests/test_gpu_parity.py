@@ -387,3 +387,30 @@ def test_gated_lookups_are_counted_out(dk):
     assert st["lookups_skipped"] == expected
     assert st["atom_updates"] == upd - expected
     dk.release_batch(bid)
+
+
+def test_out_of_memory_is_an_error_and_the_context_recovers(dk):
+    """A run whose scratch cannot fit the GPU (16 pockets x 30,000 ligands x 4,096 poses: about 0.8 TB of
+    per-pose coordinates) fails with DOCK_ERR_OUT_OF_MEMORY before any launch; the same context then docks a
+    small batch with the results of the module's context. It runs in a context of its own, so that the
+    shared one keeps its small scratch."""
+    from paper_1901_06363_gb300 import DOCK_ERR_OUT_OF_MEMORY, Docker, DockError
+    pk = synth.pocket(14, 48, 0.5, C.ELLIPSOID)
+    own = Docker(0)
+    pid = own.init_pocket(pk)
+    big = C.sweep_batch(30000)
+    bid = own.upload_ligands(big)
+    with pytest.raises(DockError) as ei:
+        own.run(bid, [pid] * 16, C.knobs(n_poses=4096), big.n, _natoms(big), xyz=False)
+    assert ei.value.code == DOCK_ERR_OUT_OF_MEMORY, str(ei.value)
+    own.release_batch(bid)
+    b = synth.ligand_batch(3, np.array([12, 30]), np.array([2, 4]))
+    kn = C.knobs(n_poses=16, repetitions=2, seed=4)
+    sb = own.upload_ligands(b)
+    res, xyz = own.run(sb, [pid], kn, b.n, _natoms(b))
+    own.close()
+    fp = dk.init_pocket(pk)
+    fb = dk.upload_ligands(b)
+    res2, xyz2 = dk.run(fb, [fp], kn, b.n, _natoms(b))
+    dk.release_batch(fb)
+    assert np.array_equal(res.view(np.int32), res2.view(np.int32)) and np.array_equal(xyz, xyz2)
