@@ -44,7 +44,9 @@ extern "C" {
 #define DOCK_ERR_TOPOLOGY (-2)      /* a rotatable bond does not split its ligand in two */
 #define DOCK_ERR_OUT_OF_MEMORY (-3) /* a device allocation failed */
 #define DOCK_ERR_CUDA (-4)          /* a CUDA runtime call failed (text in dock_last_error) */
-#define DOCK_ERR_TIMEOUT (-5)       /* a bounded device-side wait gave up */
+#define DOCK_ERR_TIMEOUT (-5)       /* reserved for a bounded device-side wait that gives up; no kernel of this
+                                       library waits on a flag (its work queue is one atomic counter), so no
+                                       call returns it */
 #define DOCK_ERR_UNSUPPORTED (-6)   /* a knob combination the library does not run */
 
 /* largest ligand (atoms) and the largest grid edge (voxels) */

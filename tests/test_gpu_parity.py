@@ -177,6 +177,13 @@ def test_error_paths(dk):
                                   np.zeros(0, np.int32))
     with pytest.raises(DockError):
         dk.upload_ligands(bad_atoms)
+    # a ligand larger than DOCK_MAX_ATOMS (255) is refused
+    n = 256
+    chain = synth.LigandBatch([0, n], [0, n - 1], [0, 0], np.stack([np.arange(n) * 1.5, np.zeros(n), np.zeros(n)], 1),
+                              np.stack([np.arange(n - 1), np.arange(1, n)], 1), np.zeros(0, np.int32))
+    with pytest.raises(DockError) as ei:
+        dk.upload_ligands(chain)
+    assert ei.value.code == DOCK_ERR_INVALID_ARG and "256 atoms" in str(ei.value)
     # non-finite and huge coordinates are refused before anything reaches the device, by both entry points
     for v in (np.nan, np.inf, -np.inf, 2e5):
         x = b.xyz.copy()
