@@ -209,6 +209,15 @@ __device__ __forceinline__ float2 angle_at(const float4* t, int j) {
     return (j & 1) ? make_float2(v.y, v.w) : make_float2(v.x, v.z);
 }
 __device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+// Square root for the circle bounds of the bump check only: x * rsqrt(x) is within about 2^-22 relative
+// of sqrt(x), the order of the FP32 rounding already in x. Near the threshold (2 A = 4 grid units at
+// h = 0.5 A) and for atoms up to 2^8 grid units from the axis, the bound (rho - r)^2 + (t - h)^2 moves
+// by under 1e-3 grid^2, inside its 0.05 margin: the same pairs go on to the per-angle tests (and
+// results are bit-identical to those with sqrtf). Non-positive x (an atom on the axis) gives ~1e-15.
+__device__ __forceinline__ float bound_sqrt(float x) {
+    x = fmaxf(x, 1e-30f);
+    return x * rsqrtf(x);
+}
 
 // Eq. 1's inner minimum taken over the probe points themselves, at grid
 // position t shifted by +0.5 (points stored shifted alike), floored at 1.
@@ -739,7 +748,7 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                                         float3 x = ld3(xs, mov[im], G, ps);
                                         float vx = x.x - gc.x, vy = x.y - gc.y, vz = x.z - gc.z;
                                         float t = kax.x * vx + kax.y * vy + kax.z * vz;
-                                        r[j] = sqrtf(fmaxf(vx * vx + vy * vy + vz * vz - t * t, 0.f));
+                                        r[j] = bound_sqrt(vx * vx + vy * vy + vz * vz - t * t);
                                         h[j] = t;
                                     }
                                 }
@@ -751,15 +760,16 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                                     {
                                         const float wx = y0.x - gc.x, wy = y0.y - gc.y, wz = y0.z - gc.z;
                                         const float t0 = kax.x * wx + kax.y * wy + kax.z * wz;
-                                        const float rho0 = sqrtf(fmaxf(wx * wx + wy * wy + wz * wz - t0 * t0, 0.f));
+                                        const float rho0 = bound_sqrt(wx * wx + wy * wy + wz * wz - t0 * t0);
                                         const float vx = y1.x - gc.x, vy = y1.y - gc.y, vz = y1.z - gc.z;
                                         const float t1 = kax.x * vx + kax.y * vy + kax.z * vz;
-                                        const float rho1 = sqrtf(fmaxf(vx * vx + vy * vy + vz * vz - t1 * t1, 0.f));
+                                        const float rho1 = bound_sqrt(vx * vx + vy * vy + vz * vz - t1 * t1);
                                         // two moving atoms per packed operation: (rho - r)^2 + (t - h)^2 with the
                                         // roundings of the scalar form (a subtraction is the addition of the negation)
                                         const float2 R0 = dup2(rho0), T0 = dup2(t0), R1 = dup2(rho1), T1 = dup2(t1);
 #pragma unroll
                                         for (int j = 0; j < 8; j += 2) {
+                                            if (j >= nslot - s0) break;  // the block's empty slots (warp-uniform)
                                             const float2 nr = make_float2(-r[j], -r[j + 1]), nh = make_float2(-h[j], -h[j + 1]);
                                             const float2 dr0 = __fadd2_rn(R0, nr), dh0 = __fadd2_rn(T0, nh);
                                             const float2 dr1 = __fadd2_rn(R1, nr), dh1 = __fadd2_rn(T1, nh);
