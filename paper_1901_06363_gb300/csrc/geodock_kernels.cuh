@@ -209,11 +209,14 @@ __device__ __forceinline__ float2 angle_at(const float4* t, int j) {
     return (j & 1) ? make_float2(v.y, v.w) : make_float2(v.x, v.z);
 }
 __device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
-// Square root for the circle bounds of the bump check only: x * rsqrt(x) is within about 2^-22 relative
-// of sqrt(x), the order of the FP32 rounding already in x. Near the threshold (2 A = 4 grid units at
-// h = 0.5 A) and for atoms up to 2^8 grid units from the axis, the bound (rho - r)^2 + (t - h)^2 moves
-// by under 1e-3 grid^2, inside its 0.05 margin: the same pairs go on to the per-angle tests (and
-// results are bit-identical to those with sqrtf). Non-positive x (an atom on the axis) gives ~1e-15.
+// Square root for the two pruning bounds only (never for a value that enters a result): x * rsqrt(x) is
+// within about 2^-22 relative of sqrt(x), the order of the FP32 rounding already in x.
+//  - circle bounds of the bump check: near the threshold (2 A = 4 grid units at h = 0.5 A) and for atoms
+//    up to 2^8 grid units from the axis, (rho - r)^2 + (t - h)^2 moves by under 1e-3 grid^2, inside the
+//    bound's 0.05 margin, so the same pairs go on to the per-angle tests;
+//  - a moving atom's circle inside the padded box: its radius moves by under 1e-4 grid units, inside the
+//    test's 1e-3 margin, so the unchecked lookup path is taken only where it is safe.
+// Non-positive x (an atom on the axis) gives about 1e-15.
 __device__ __forceinline__ float bound_sqrt(float x) {
     x = fmaxf(x, 1e-30f);
     return x * rsqrtf(x);
@@ -788,8 +791,8 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                                         const int e = __ffsll(pairs) - 1;
                                         pairs &= pairs - 1;
                                         const float3 y = e < 8 ? y0 : y1;
-                                        const Split sp =
-                                            turn(split(ld3(xs, mov[q + Q * (s0 + (e & 7))], G, ps), gc, kax), pre);
+                                        const Split sp0 = split(ld3(xs, mov[q + Q * (s0 + (e & 7))], G, ps), gc, kax);
+                                        const Split sp = peel ? turn(sp0, pre) : sp0;
                                         // d^2(theta) = A + B cos(theta) + C sin(theta) at every candidate
                                         const float dx = sp.a.x - y.x, dy = sp.a.y - y.y, dz = sp.a.z - y.z;
                                         const float A = dx * dx + dy * dy + dz * dz +
@@ -799,16 +802,19 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                                         // candidates 12 at a time, two per packed multiply-add; a block
                                         // may straddle two 64-bit words
                                         const float4* tw = reinterpret_cast<const float4*>(ptab);
-                                        const float2 A2 = dup2(A), B2 = dup2(B), C2 = dup2(C);
+                                        // the test is the sign bit of (A - thr^2) + B cos + C sin (FP32, two
+                                        // candidates per packed multiply-add); the bits are shifted in from the
+                                        // block's last candidate down to its first
+                                        const float2 A2 = dup2(A - thr2), B2 = dup2(B), C2 = dup2(C);
                                         for (int g = 0; g < ncand; g += 12) {
                                             unsigned m12 = 0;
 #pragma unroll
-                                            for (int k = 0; k < 6; ++k) {
+                                            for (int k = 5; k >= 0; --k) {
                                                 const float4 t = tw[(g >> 1) + k];
                                                 const float2 d2 = __ffma2_rn(C2, make_float2(t.z, t.w),
                                                                              __ffma2_rn(B2, make_float2(t.x, t.y), A2));
-                                                if (d2.x < thr2) m12 |= 1u << (2 * k);
-                                                if (d2.y < thr2) m12 |= 2u << (2 * k);
+                                                m12 = __funnelshift_l(__float_as_uint(d2.y), m12, 1);
+                                                m12 = __funnelshift_l(__float_as_uint(d2.x), m12, 1);
                                             }
                                             const int w = g >> 6, sh = g & 63;
                                             col[w * 32] |= (unsigned long long)m12 << sh;
@@ -848,7 +854,7 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                             }
 
                             auto circle_inside = [&](const Split& sp) {
-                                const float rad = sqrtf(sp.u.x * sp.u.x + sp.u.y * sp.u.y + sp.u.z * sp.u.z) + 1e-3f;
+                                const float rad = bound_sqrt(sp.u.x * sp.u.x + sp.u.y * sp.u.y + sp.u.z * sp.u.z) + 1e-3f;
                                 return sp.a.x - rad >= lo && sp.a.x + rad < hix && sp.a.y - rad >= lo &&
                                        sp.a.y + rad < hiy && sp.a.z - rad >= lo && sp.a.z + rad < hiz;
                             };
@@ -858,7 +864,8 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                             for (; s < nslot; ++s) {
                                 const int i0 = q + Q * s;
                                 const bool h0 = i0 < nmov;
-                                Split one[1] = {turn(split(ld3(xs, mov[h0 ? i0 : 0], G, ps), gc, kax), pre)};
+                                const Split one0 = split(ld3(xs, mov[h0 ? i0 : 0], G, ps), gc, kax);
+                                Split one[1] = {peel ? turn(one0, pre) : one0};
                                 const bool fast = __all_sync(FULL, !h0 || !work || circle_inside(one[0]));
                                 // a pose not computed in this repetition makes no lookups (its lane idles)
                                 if (h0 && work) score_atoms<KC, MODE, CLIP, 1>(pd, K, one, fast, cst, acc, pen, box, need);
