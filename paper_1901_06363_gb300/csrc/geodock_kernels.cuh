@@ -652,12 +652,10 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                     const uint8_t* fix = sidx + sd.nmov;
                     const int nmov = sd.nmov, nfixB = sd.nfixB;
                     const int nslot = (nmov + Q - 1) / Q;  // moving atoms per lane (q + Q*s)
-                    float* tS = nullptr;
-                    int* tSt = nullptr;
                     if (P.trace_on && active) {
-                        int64_t ci = (tbase + sweep) * P.tr.pmax;
-                        tS = P.tr.cand_S + ci;
-                        tSt = P.tr.cand_status + ci;
+                        const int64_t ci = (tbase + sweep) * P.tr.pmax;
+                        float* tS = P.tr.cand_S + ci;
+                        int* tSt = P.tr.cand_status + ci;
                         for (int j = q; j < P.tr.pmax; j += Q) {
                             tS[j] = 0.f;
                             tSt[j] = -2;
@@ -695,7 +693,6 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                     }
 
                     unsigned long long best = make_key(S_inc, 0);
-                    const float2* cs = coarse ? P.cs_lp : P.cs_hp;
                     const int phases = peel ? 2 : 1;
                     int tile_first = 0;
                     bool have_tile = true;  // a pose with no feasible tile centre keeps its incumbent
@@ -706,7 +703,7 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                         const float2* tab;
                         if (!peel) {
                             ncand = (coarse ? P.P_lp : P.P_hp) - 1;
-                            tab = cs + 1;
+                            tab = (coarse ? P.cs_lp : P.cs_hp) + 1;
                             slot0 = 1;
                         } else if (ph == 0) {
                             ncand = P.n_tiles;
@@ -910,8 +907,11 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                                 const unsigned long long key = make_key(S, slot0 + j0 + j);
                                 pbest = (ok && key < pbest) ? key : pbest;
                             }
-                            if (tS && q == 0) {
+                            if (P.trace_on && active && q == 0) {
                                 // trace: every evaluated candidate's S and status
+                                const int64_t ci = (tbase + sweep) * P.tr.pmax;
+                                float* tS = P.tr.cand_S + ci;
+                                int* tSt = P.tr.cand_status + ci;
 #pragma unroll 1
                                 for (int j = 0; j < nvalid; ++j) {
                                     if (!have_tile) break;
@@ -944,7 +944,7 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                     const int kb = work ? (int)(best & 0xffffffffu) : 0;
                     if (kb != 0) {
                         // the same rotation as the candidate's evaluation
-                        const float2 v = !peel ? cs[kb] : P.cs_hp[kb - 1 - P.n_tiles];
+                        const float2 v = !peel ? (coarse ? P.cs_lp : P.cs_hp)[kb] : P.cs_hp[kb - 1 - P.n_tiles];
                         const float2 r0 = !peel ? make_float2(1.f, 0.f) : pre;
                         for (int s = 0; s < nslot; ++s) {
                             const int im = q + Q * s;
