@@ -166,7 +166,11 @@ void dock_destroy(dock_ctx* ctx);
 const char* dock_last_error(const dock_ctx* ctx);
 
 /* Upload a pocket and build its field K on the GPU (Eq. 1, inner minimum),
- * unless p->K is given. *pocket_id receives its handle. Synchronous. */
+ * unless p->K is given. *pocket_id receives its handle. Synchronous. The
+ * pocket holds, on the device, K (2 bytes per voxel), a padded 32-bit copy
+ * for nearest-voxel lookups ((n+32)^3 x 4 bytes) and the 2x2x2 corners of
+ * every voxel for the trilinear score (16 bytes per voxel): about 54 MB for
+ * a 128^3 grid, 8.2 MB for 64^3. */
 int dock_init_pocket(dock_ctx* ctx, const dock_pocket* p, int* pocket_id);
 
 /* Copy a pocket's field back to host memory K (nx*ny*nz uint16, x fastest). */
@@ -295,7 +299,7 @@ int dock_autotune(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs* 
  *   lookups_skipped  (candidate, moving atom) lookups not made because the
  *                    bump check had already rejected every candidate of
  *                    their block of angles for every pose computed in the
- *                    warp (nearest-voxel score) */
+ *                    warp (nearest-voxel and trilinear scores) */
 typedef struct {
     uint64_t candidates;
     uint64_t atom_updates;

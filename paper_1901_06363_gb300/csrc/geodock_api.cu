@@ -76,6 +76,7 @@ struct PocketH {
     PocketDev d{};
     std::unique_ptr<DevBuf> K;
     std::unique_ptr<FieldTex> Kt;
+    std::unique_ptr<FieldTex> Kc;  // corner texture of the trilinear score
     std::unique_ptr<DevBuf> dev;  // device copy of d
     std::unique_ptr<DevBuf> pts;  // probe points for the exact score (float4, voxel + 0.5)
 };
@@ -717,6 +718,34 @@ int dock_init_pocket(dock_ctx* ctx, const dock_pocket* p, int* pocket_id) {
         CK(cudaCreateTextureObject(&ph.Kt->tex, &rd, &td, nullptr));
         CK(cudaDeviceSynchronize());  // before the linear copy is freed
     }
+    // the 2x2x2 corners of every voxel, one 16-byte texel each, for the trilinear score
+    {
+        DevBuf lin;
+        CK(lin.ensure(nv * sizeof(uint4)));
+        corner_field_kernel<<<(unsigned)((nv + 255) / 256), 256>>>(lin.as<uint4>(), ph.K->as<uint16_t>(), p->nx, p->ny,
+                                                                   p->nz);
+        CK(cudaGetLastError());
+        CK(cudaDeviceSynchronize());
+        ph.Kc.reset(new FieldTex());
+        cudaChannelFormatDesc fd = cudaCreateChannelDesc<uint4>();
+        CK(cudaMalloc3DArray(&ph.Kc->arr, &fd, make_cudaExtent(p->nx, p->ny, p->nz)));
+        cudaMemcpy3DParms cp = {};
+        cp.srcPtr = make_cudaPitchedPtr(lin.p, (size_t)p->nx * sizeof(uint4), p->nx, p->ny);
+        cp.dstArray = ph.Kc->arr;
+        cp.extent = make_cudaExtent(p->nx, p->ny, p->nz);
+        cp.kind = cudaMemcpyDeviceToDevice;
+        CK(cudaMemcpy3D(&cp));
+        cudaResourceDesc rd = {};
+        rd.resType = cudaResourceTypeArray;
+        rd.res.array.array = ph.Kc->arr;
+        cudaTextureDesc td = {};
+        td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
+        td.filterMode = cudaFilterModePoint;
+        td.readMode = cudaReadModeElementType;
+        td.normalizedCoords = 0;
+        CK(cudaCreateTextureObject(&ph.Kc->tex, &rd, &td, nullptr));
+        CK(cudaDeviceSynchronize());  // before the linear copy is freed
+    }
     // probe points for the exact score (Eq. 1's inner minimum without the grid)
     if (p->pts && p->npts > 0) {
         std::vector<float4> q(p->npts);
@@ -734,6 +763,7 @@ int dock_init_pocket(dock_ctx* ctx, const dock_pocket* p, int* pocket_id) {
     }
     ph.d.K = ph.K->as<uint16_t>();
     ph.d.Kt = ph.Kt->tex;
+    ph.d.Kc = ph.Kc->tex;
     ph.d.nx = p->nx;
     ph.d.ny = p->ny;
     ph.d.nz = p->nz;

@@ -49,6 +49,8 @@ struct PocketDev {
     unsigned long long Kt;  // the same values padded by PAD voxels per side, OUTSIDE beyond the grid, as
                             // a 3D texture (point sampling, unnormalized coordinates): a fetch at padded
                             // position t returns the value of the voxel floor(t)
+    unsigned long long Kc;  // the 2x2x2 corners of every voxel (i..i+1 per axis, repeated at the upper edges),
+                            // eight 16-bit values per texel, as a 3D texture: one fetch per trilinear term
     const float4* pts;   // probe points (voxel index + 0.5, grid units) for the exact score; NULL if unknown
     int npts;
     int nx, ny, nz;
@@ -385,6 +387,29 @@ struct Acc<2> {
     using T = float;
 };
 
+// Trilinear term (MODE 1) from the corner texture: the voxel floor(c) of the clamped position c is fetched
+// at its centre, so the texel is the one the weights c - floor(c) refer to. At c = n - 1 exactly the
+// repeated upper corners with weight 0 give the value the lower voxel gives with weight 1.
+template <bool CLIP>
+__device__ __forceinline__ float term_tri(const PocketDev& pd, float3 t, bool* in) {
+    const float hx = (float)(pd.nx - 1), hy = (float)(pd.ny - 1), hz = (float)(pd.nz - 1);
+    *in = (t.x >= 0.f) & (t.x <= hx) & (t.y >= 0.f) & (t.y <= hy) & (t.z >= 0.f) & (t.z <= hz);
+    const float cx = fminf(fmaxf(t.x, 0.f), hx), cy = fminf(fmaxf(t.y, 0.f), hy), cz = fminf(fmaxf(t.z, 0.f), hz);
+    const float x0 = floorf(cx), y0 = floorf(cy), z0 = floorf(cz);
+    const float fx = cx - x0, fy = cy - y0, fz = cz - z0;
+    const uint4 c = tex3D<uint4>(pd.Kc, x0 + 0.5f, y0 + 0.5f, z0 + 0.5f);
+    const float c000 = (float)(c.x & 0xffffu), c100 = (float)(c.x >> 16), c010 = (float)(c.y & 0xffffu),
+                c110 = (float)(c.y >> 16), c001 = (float)(c.z & 0xffffu), c101 = (float)(c.z >> 16),
+                c011 = (float)(c.w & 0xffffu), c111 = (float)(c.w >> 16);
+    const float c00 = fmaf(fx, c100 - c000, c000), c10 = fmaf(fx, c110 - c010, c010);
+    const float c01 = fmaf(fx, c101 - c001, c001), c11 = fmaf(fx, c111 - c011, c011);
+    const float c0 = fmaf(fy, c10 - c00, c00), c1 = fmaf(fy, c11 - c01, c01);
+    const float v = fmaf(fz, c1 - c0, c0);
+    if (CLIP) return v;
+    const float ex = t.x - cx, ey = t.y - cy, ez = t.z - cz;
+    return v + (ex * ex + ey * ey + ez * ez);
+}
+
 // Nearest-voxel value with the bounds test (shifted grid position t): the value
 // of the voxel (clamped to the box when outside) and whether t is inside.
 __device__ __forceinline__ uint32_t lookup_checked(const PocketDev& pd, const uint16_t* __restrict__ K, float3 t,
@@ -500,14 +525,21 @@ __device__ __forceinline__ void score_atoms(const PocketDev& pd, const uint16_t*
             }
         }
     } else {
+        // blocks of candidates that no pose of the warp needs (all infeasible) are skipped
+        constexpr int BLK = gate_block(KC);
 #pragma unroll
-        for (int j = 0; j < KC; ++j) {
-            const float2 c = angle_at(cst, j);
+        for (int jb = 0; jb < KC; jb += BLK) {
+            if ((need >> jb) & ((1ull << BLK) - 1ull)) {
 #pragma unroll
-            for (int a = 0; a < NA; ++a) {
-                bool in;
-                acc[j] += term<1, CLIP>(pd, K, place(s[a], c.x, c.y), &in);
-                if (CLIP && !in) box |= 1ull << j;
+                for (int j = jb; j < jb + BLK && j < KC; ++j) {
+                    const float2 c = angle_at(cst, j);
+#pragma unroll
+                    for (int a = 0; a < NA; ++a) {
+                        bool in;
+                        acc[j] += term_tri<CLIP>(pd, place(s[a], c.x, c.y), &in);
+                        if (CLIP && !in) box |= 1ull << j;
+                    }
+                }
             }
         }
     }
@@ -871,7 +903,7 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                             // for every moving atom of every working pose (counted as if every pass took
                             // the fast path; the checked path scores all candidates, so this count is
                             // never below the lookups actually left out)
-                            if (MODE == 0 && P.lookups_skipped) {
+                            if (MODE != 2 && P.lookups_skipped) {
                                 const unsigned nw = __popc(__ballot_sync(FULL, work && q == 0));
                                 constexpr int BLK = gate_block(KC);
                                 const uint64_t vm = nvalid >= 64 ? ~0ull : ((1ull << nvalid) - 1ull);
@@ -1091,6 +1123,17 @@ static __global__ void field_kernel(uint16_t* K, int nx, int ny, int nz, const i
     if (v < nvox) K[v] = (uint16_t)max(best, 1);
 }
 // Padded copy of the field: PAD voxels of OUTSIDE around the grid.
+static __global__ void corner_field_kernel(uint4* Kc, const uint16_t* K, int nx, int ny, int nz) {
+    const int64_t n = (int64_t)nx * ny * nz;
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((int64_t)nx * ny));
+    const int x1 = x + 1 < nx ? x + 1 : x, y1 = y + 1 < ny ? y + 1 : y, z1 = z + 1 < nz ? z + 1 : z;
+    auto at = [&](int i, int j, int l) { return (uint32_t)K[((int64_t)l * ny + j) * nx + i]; };
+    Kc[v] = make_uint4(at(x, y, z) | (at(x1, y, z) << 16), at(x, y1, z) | (at(x1, y1, z) << 16),
+                       at(x, y, z1) | (at(x1, y, z1) << 16), at(x, y1, z1) | (at(x1, y1, z1) << 16));
+}
+
 static __global__ void pad_field_kernel(uint32_t* Kp, const uint16_t* K, int nx, int ny, int nz) {
     const int pnx = nx + 2 * PAD, pny = ny + 2 * PAD, pnz = nz + 2 * PAD;
     const int64_t n = (int64_t)pnx * pny * pnz;

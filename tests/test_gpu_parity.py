@@ -351,16 +351,18 @@ def test_fixed_point_repetitions_are_counted_out(dk, n_grid):
     dk.release_batch(bid)
 
 
-def test_gated_lookups_are_counted_out(dk):
+@pytest.mark.parametrize("score_mode", [0, 1])
+def test_gated_lookups_are_counted_out(dk, score_mode):
     """Blocks of 6 candidates that the bump check rejected for every working pose of a warp are not scored; the
     count of lookups left out equals a replay of that rule on the traced run's candidate statuses (ligands of at
     most 32 atoms and 16 poses: one warp of 2 lanes per pose per ligand; 30 degrees: 11 candidates, blocks
-    [0, 6) and [6, 11))."""
+    [0, 6) and [6, 11)), for the nearest-voxel and the trilinear score."""
     import indep
     pk = synth.pocket(8, 64, 0.5, C.ELLIPSOID)
     l, t = synth.ligand_sizes(23, 24, 0, [16, 32, 1, 6])
     b = synth.ligand_batch(23, l, t)
-    kn = C.knobs(n_poses=16, hp_step=30.0, lp_step=30.0, repetitions=3, bump_thr=2.6, seed=2)
+    kn = C.knobs(n_poses=16, hp_step=30.0, lp_step=30.0, repetitions=3, bump_thr=2.6, seed=2,
+                 score_mode=score_mode)
     pid = dk.init_pocket(pk)
     bid = dk.upload_ligands(b)
     res, _ = dk.run(bid, [pid], kn, b.n, _natoms(b))
