@@ -263,7 +263,8 @@ int dock_run_trace(dock_ctx* ctx, int batch_id, int pocket_id, const dock_knobs*
 int dock_trace_pmax(const dock_knobs* k);
 
 /* Tile shape of the sweep kernel. lanes_per_pose (1, 2, 4, 8) lanes share a
- * pose and split its angles; angles_per_chunk (8, 12, 18, 36) angles a lane
+ * pose and split its moving atoms (a ligand whose poses would not fit the
+ * warp's coordinate slice gets more); angles_per_chunk (8, 12, 18, 36) angles a lane
  * keeps in registers; warps_per_cta. dock_set_tile forces a shape for the
  * batched form (0 fields keep the current choice); dock_autotune times the
  * shapes on a sample of the batch and keeps the fastest for (batch, knobs). */
