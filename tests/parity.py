@@ -26,7 +26,8 @@ end of a run, 1.4e-4 Å at most over the GPU suite). A nearest voxel can
 differ only for an atom that close to a voxel face, far inside the band of
 1e-3 voxel. A squared distance near thr^2 = (2 Å)^2 moves by at most about
 2 * 2 Å * (the drift of the pair's difference) plus the FP32 rounding of
-A + B cos + C sin (under 1e-5 Å^2): about 2e-4 Å^2 for a typical drift of
+the GPU's test value (A - thr^2) + B cos + C sin, whose sign decides (under
+1e-5 Å^2): about 2e-4 Å^2 for a typical drift of
 5e-5 Å. The band of 4e-4 Å^2 is the parity protocol's; over the GPU suite's
 75 million compared candidates every feasibility difference lay inside it
 (the suite prints the counts).
