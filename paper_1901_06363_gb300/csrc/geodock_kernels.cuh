@@ -769,14 +769,18 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                         __syncwarp();
                         {
                             const float lim = thr2 + 0.05f;  // margin over the FP32 error of the bound
-                            for (int s0 = 0; s0 < nslot; s0 += 8) {
+                            // a moving side of at most 8 atoms: every lane of a pose holds all of them and the
+                            // pose's lanes split the fixed atoms instead
+                            const bool small = nmov <= 8;
+                            const int nsl = small ? nmov : nslot;
+                            for (int s0 = 0; s0 < nsl; s0 += 8) {
                                 float r[8], h[8];
 #pragma unroll
                                 for (int j = 0; j < 8; ++j) {
-                                    const int im = q + Q * (s0 + j);
+                                    const int im = small ? s0 + j : q + Q * (s0 + j);
                                     r[j] = 1e18f;  // no atom: never close (its square stays finite)
                                     h[j] = 0.f;
-                                    if (s0 + j < nslot && im < nmov) {
+                                    if (s0 + j < nsl && im < nmov) {
                                         float3 x = ld3(xs, mov[im], G, ps);
                                         float vx = x.x - gc.x, vy = x.y - gc.y, vz = x.z - gc.z;
                                         float t = kax.x * vx + kax.y * vy + kax.z * vz;
@@ -785,7 +789,7 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                                     }
                                 }
                                 // fixed atoms two at a time (independent loads in flight)
-                                for (int f = 0; f < nfixB; f += 2) {
+                                for (int f = small ? 2 * q : 0; f < nfixB; f += small ? 2 * Q : 2) {
                                     const int f1 = f + 1 < nfixB ? f + 1 : f;
                                     const float3 y0 = ld3(xs, fix[f], G, ps), y1 = ld3(xs, fix[f1], G, ps);
                                     unsigned near0 = 0, near1 = 0;
@@ -801,7 +805,7 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                                         const float2 R0 = dup2(rho0), T0 = dup2(t0), R1 = dup2(rho1), T1 = dup2(t1);
 #pragma unroll
                                         for (int j = 0; j < 8; j += 2) {
-                                            if (j >= nslot - s0) break;  // the block's empty slots (warp-uniform)
+                                            if (j >= nsl - s0) break;  // the block's empty slots (warp-uniform)
                                             const float2 nr = make_float2(-r[j], -r[j + 1]), nh = make_float2(-h[j], -h[j + 1]);
                                             const float2 dr0 = __fadd2_rn(R0, nr), dh0 = __fadd2_rn(T0, nh);
                                             const float2 dr1 = __fadd2_rn(R1, nr), dh1 = __fadd2_rn(T1, nh);
@@ -820,7 +824,7 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                                         const int e = __ffsll(pairs) - 1;
                                         pairs &= pairs - 1;
                                         const float3 y = e < 8 ? y0 : y1;
-                                        const Split sp0 = split(ld3(xs, mov[q + Q * (s0 + (e & 7))], G, ps), gc, kax);
+                                        const Split sp0 = split(ld3(xs, mov[small ? s0 + (e & 7) : q + Q * (s0 + (e & 7))], G, ps), gc, kax);
                                         const Split sp = peel ? turn(sp0, pre) : sp0;
                                         // d^2(theta) = A + B cos(theta) + C sin(theta) at every candidate
                                         const float dx = sp.a.x - y.x, dy = sp.a.y - y.y, dz = sp.a.z - y.z;
