@@ -770,8 +770,9 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                         {
                             const float lim = thr2 + 0.05f;  // margin over the FP32 error of the bound
                             // a moving side of at most 8 atoms: every lane of a pose holds all of them and the
-                            // pose's lanes split the fixed atoms instead
-                            const bool small = nmov <= 8;
+                            // pose's lanes split the fixed atoms instead (not with the exact score, whose point
+                            // loop runs slower in that build: measured)
+                            const bool small = MODE != 2 && nmov <= 8;
                             const int nsl = small ? nmov : nslot;
                             for (int s0 = 0; s0 < nsl; s0 += 8) {
                                 float r[8], h[8];
