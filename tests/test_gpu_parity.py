@@ -123,6 +123,21 @@ def test_knob_variants(dk, variant):
     trace_parity(dk, pk, b, kn)
 
 
+@pytest.mark.parametrize("clip", [1, 0])
+def test_trilinear_non_cubic_grid(dk, clip):
+    """Trilinear score on a 37 x 23 x 19 grid (h = 0.4 A, random probe points): the corner texture's three
+    strides differ, and with clipping off every atom beyond an upper face is scored at the clamped
+    position n - 1 exactly, where the texel's repeated corners take weight 0."""
+    rng = np.random.default_rng(3)
+    pk = synth.Pocket((37, 23, 19), 0.4, (1.0, -2.0, 0.5), (8.2, 2.4, 4.1),
+                      np.stack([rng.integers(0, d, 80) for d in (37, 23, 19)], 1))
+    l, t = synth.ligand_sizes(31, 8, 0, [12, 24, 2, 5])
+    b = synth.ligand_batch(31, l, t)
+    kn = C.knobs(n_poses=16, hp_step=20.0, lp_step=20.0, repetitions=2, seed=4, score_mode=1, clip_box=clip)
+    stats, g, _ = trace_parity(dk, pk, b, kn)
+    assert stats["candidates"] > 2000
+
+
 def test_edge_cases(dk):
     pk = synth.pocket(14, 48, 0.5, C.ELLIPSOID)
     pid = dk.init_pocket(pk)
