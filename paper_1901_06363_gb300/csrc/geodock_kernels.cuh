@@ -350,15 +350,18 @@ constexpr int BW = 7;
 // bytes; the area's last word holds the warp's count of gated lookups): the
 // rest of the SM's shared memory serves as L1 cache for the field lookups.
 constexpr int IDX_FLOATS = 68;
+// per pose slot of the warp: its score (-1 if it started outside the box) while its lanes serve other
+// poses (the remap of working poses onto more lanes, below)
+constexpr int POSE_FLOATS = 32;
 // Entries of the phase's angle table past 64 bw: a chunk's worth for the
 // lookups, and the 12-candidate blocks of the bump tests.
 __host__ __device__ constexpr int ptab_pad(int kc) { return kc > 12 ? kc : 12; }
 __host__ __device__ constexpr int warp_extra_floats(int kc, int bw) {
-    return bw * 64 + 2 * (64 * bw + ptab_pad(kc)) + IDX_FLOATS;
+    return bw * 64 + 2 * (64 * bw + ptab_pad(kc)) + IDX_FLOATS + POSE_FLOATS;
 }
 // every warp's area starts on a 16-byte boundary (the angle table is read as float4): slices are multiples
 // of 4 floats, and so are these parts
-static_assert(IDX_FLOATS % 4 == 0 && (2 * ptab_pad(8)) % 4 == 0 && (2 * ptab_pad(18)) % 4 == 0 &&
+static_assert(IDX_FLOATS % 4 == 0 && POSE_FLOATS % 4 == 0 && (2 * ptab_pad(8)) % 4 == 0 && (2 * ptab_pad(18)) % 4 == 0 &&
                   (2 * ptab_pad(36)) % 4 == 0,
               "per-warp shared-memory areas keep 16-byte alignment");
 
@@ -559,6 +562,7 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
     // the last word of the index-list area (lists take at most 258 bytes): the warp's count of
     // lookups left out by the gate in the current task
     unsigned* wlook = reinterpret_cast<unsigned*>(sidx) + (IDX_FLOATS - 1);
+    float* smS = reinterpret_cast<float*>(sidx) + IDX_FLOATS;  // [32] pose scores (-1: not live)
     const float shift = MODE == 1 ? 0.0f : 0.5f;
 
     for (;;) {
@@ -567,11 +571,11 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
         task = __shfl_sync(FULL, task, 0);
         if (task >= P.ntask) break;
         const int2 tk = P.tasks[task];
-        const int lq = tk.y >> 16;
-        const int Q = 1 << lq;       // lanes per pose (they split the pose's atoms)
-        const int G = 32 >> lq;      // poses of this warp
-        const int ps = lane >> lq;   // pose slot
-        const int q = lane & (Q - 1);
+        int lq = tk.y >> 16;
+        int Q = 1 << lq;             // lanes per pose (they split the pose's atoms)
+        const int G = 32 >> lq;      // poses of this warp (columns of its coordinate slice)
+        int ps = lane >> lq;         // pose slot
+        int q = lane & (Q - 1);
         const int pocket = tk.x / P.nlig, b = tk.x % P.nlig;
 #ifdef GEODOCK_CHECKED
         if (!GD_OK(P.check, pocket < P.npockets, 7, pocket)) continue;
@@ -585,7 +589,7 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
         const uint16_t* __restrict__ K = pd.K;
         const LigDev L = P.lig[b];
         const int p = (tk.y & 0xffff) * G + ps;
-        const bool active = p < P.n_poses;
+        bool active = p < P.n_poses;
         const float thr_g = (float)(P.bump_thr / pd.h);
         const float thr2 = thr_g * thr_g;
         const float nxf = (float)pd.nx, nyf = (float)pd.ny, nzf = (float)pd.nz;
@@ -628,7 +632,7 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
         }
         S_inc = group_sum(S_inc, Q);
         inbox = group_all(inbox, Q);
-        const bool live = active && (!CLIP || inbox);
+        bool live = active && (!CLIP || inbox);
         const int nsweep = P.repetitions * L.nside;
         // trace layout: n_poses * repetitions * (sweeps of earlier ligands) + p * nsweep
         const int64_t tbase = (int64_t)P.n_poses * P.repetitions * L.side_off + (int64_t)p * nsweep;
@@ -650,11 +654,47 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
         // whose poses are all at a fixed point stops. nskip counts the pose-repetitions left out; a
         // pose that starts outside the box computes none.
         bool conv = !live;
+        // pose-repetitions left out: with nearest-voxel values, counted for the warp (per repetition its
+        // active poses less those computed, as poses move between lanes); otherwise by each pose's first
+        // lane (the exact score's point loop runs slower with the warp-wide count: measured)
+        const unsigned nact = (unsigned)max(0, min(G, P.n_poses - (tk.y & 0xffff) * G));
         unsigned nskip = 0;
+        bool remapped = false;
         if (lane == 0) *wlook = 0u;
         if (__any_sync(FULL, live)) {
             for (int rep = 0; rep < P.repetitions; ++rep) {
                 bool moved = false;  // did this pose commit any angle in this repetition
+                const unsigned wm = __ballot_sync(FULL, live && !conv && q == 0);  // leaders of working poses
+                const int nwork = __popc(wm);
+                if (MODE == 0) nskip += nact - (unsigned)nwork;
+                if (MODE == 0 && !P.trace_on && rep > 0) {
+                    // The poses still working take over the lanes of those at a fixed point: each gets the
+                    // most lanes (a power of two) that lets all of them fit the warp. A pose's coordinates
+                    // stay in its slice column; its score moves with it. With nearest-voxel values every
+                    // sum is an exact integer, so the results do not depend on the lanes a pose runs on.
+                    int lqn = lq;
+                    while (lqn < 5 && (nwork << (lqn + 1)) <= 32) ++lqn;
+                    if (lqn > lq && nwork > 0) {
+                        if (q == 0 && active) smS[ps] = live ? S_inc : -1.f;
+                        const int j = lane >> lqn;
+                        const bool asg = j < nwork;
+                        unsigned mk = wm;  // the j-th working leader: drop the j lowest set bits
+                        for (int t = 0; t < j && mk; ++t) mk &= mk - 1u;
+                        const int leader = asg ? __ffs(mk) - 1 : 0;
+                        const int psn = __shfl_sync(FULL, ps, leader);
+                        const float Sn = __shfl_sync(FULL, S_inc, leader);
+                        __syncwarp();
+                        remapped = true;
+                        lq = lqn;
+                        Q = 1 << lq;
+                        q = lane & (Q - 1);
+                        ps = asg ? psn : 0;
+                        S_inc = Sn;
+                        active = asg;
+                        live = asg;
+                        conv = !asg;
+                    }
+                }
                 const bool work = live && !conv;
                 for (int si = 0; si < L.nside; ++si) {
                     const SideDev sd = P.side[L.side_off + si];
@@ -998,21 +1038,36 @@ __global__ void __launch_bounds__(256, KC <= 18 ? 2 : 1) sweep_kernel(SweepParam
                 }
                 // a repetition in which no pose of the warp moved left every pose where it was, so
                 // each further repetition would repeat it exactly: stop (the trace records them all)
-                if (conv && active && q == 0) ++nskip;
+                if (MODE != 0 && conv && active && q == 0) ++nskip;
                 if (!P.trace_on && !moved) conv = true;
                 if (!P.trace_on && !__any_sync(FULL, moved)) {
-                    if (active && q == 0) nskip += (unsigned)(P.repetitions - 1 - rep);
+                    if (MODE == 0) nskip += (unsigned)(P.repetitions - 1 - rep) * nact;
+                    else if (active && q == 0) nskip += (unsigned)(P.repetitions - 1 - rep);
                     break;
                 }
             }
-        } else if (active && q == 0) {
-            nskip = (unsigned)P.repetitions;
+        } else {
+            if (MODE == 0) nskip = (unsigned)P.repetitions * nact;
+            else if (active && q == 0) nskip = (unsigned)P.repetitions;
         }
-        if (P.skipped) {
+        if (remapped) {
+            // every pose back in its own lanes, with its score
+            if (q == 0 && active) smS[ps] = live ? S_inc : -1.f;
+            __syncwarp();
+            lq = tk.y >> 16;
+            Q = 1 << lq;
+            ps = lane >> lq;
+            q = lane & (Q - 1);
+            active = (tk.y & 0xffff) * G + ps < P.n_poses;
+            const float sv = active ? smS[ps] : -1.f;
+            live = sv >= 0.f;
+            S_inc = sv;
+        }
+        if (MODE != 0) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) nskip += __shfl_xor_sync(FULL, nskip, o);
-            if (lane == 0 && nskip) atomicAdd(P.skipped + tk.x, nskip);
         }
+        if (P.skipped && lane == 0 && nskip) atomicAdd(P.skipped + tk.x, nskip);
         if (P.lookups_skipped && lane == 0 && *wlook) atomicAdd(P.lookups_skipped, (unsigned long long)*wlook);
         // ---- per-pose result
         if (active && q == 0 &&
