@@ -264,7 +264,10 @@ int dock_trace_pmax(const dock_knobs* k);
 
 /* Tile shape of the sweep kernel. lanes_per_pose (1, 2, 4, 8) lanes share a
  * pose and split its moving atoms (a ligand whose poses would not fit the
- * warp's coordinate slice gets more); angles_per_chunk (8, 12, 18, 36) angles a lane
+ * warp's coordinate slice gets more, and so, with the nearest-voxel score
+ * and lanes_per_pose not forced, does a ligand whose pose group would
+ * outlast the average load of the launch's warps); angles_per_chunk (8, 12,
+ * 18, 36) angles a lane
  * keeps in registers; warps_per_cta. dock_set_tile forces a shape for the
  * batched form (0 fields keep the current choice); dock_autotune times the
  * shapes on a sample of the batch and keeps the fastest for (batch, knobs). */

@@ -1077,7 +1077,8 @@ int build_plan(dock_ctx* ctx, const BatchH& B, const int32_t* pids, int np, cons
 // Build (or fetch) the plan of a run: pockets, angle tables, tasks, launch shape.
 int get_plan(dock_ctx* ctx, int batch_id, const int32_t* pids, int np, const dock_knobs* k, int plain, Plan** out) {
     const dock_tile t = resolve_tile(ctx, batch_id, k);
-    std::string key = plan_key(batch_id, pids, np, k, t, plain);
+    // a forced lanes_per_pose also turns off the split of heavy ligands (build_plan), so it is part of the key
+    const std::string key = plan_key(batch_id, pids, np, k, t, plain) + (ctx->tile.lanes_per_pose ? "forced" : "");
     auto it = ctx->plans.find(key);
     if (it != ctx->plans.end()) {
         *out = it->second.get();
@@ -1133,12 +1134,38 @@ int build_plan(dock_ctx* ctx, const BatchH& B, const int32_t* pids, int np, cons
     std::vector<double> cost;
     pl->task_off.assign(pl->npairs + 1, 0);
     const Steps st = steps_of(k);
+    std::vector<int> lqs(B.n);
+    std::vector<double> cb(B.n);
+    for (int b = 0; b < B.n; ++b) {
+        lqs[b] = lanes_log2(t, pl->slice, B.l[b]);
+        cb[b] = task_cost(B, b, k, st, 1 << lqs[b], pl->kc);
+    }
+    // A launch lasts at least as long as its longest task. With the nearest-voxel score (exact integer
+    // sums: results do not depend on the lanes a pose runs on), a ligand whose task would cost more than
+    // 0.8 of the average load of a warp slot gets twice the lanes per pose (half the poses per task),
+    // again while that holds: the heaviest ligands of a batch, or every ligand of a small batch. A
+    // lanes_per_pose forced by dock_set_tile is kept as it is.
+    if (!plain && k->score_mode == 0 && !ctx->tile.lanes_per_pose) {
+        const double slots = (double)(pl->kc <= 18 ? 2 : 1) * ctx->num_sms * pl->W;
+        for (int pass = 0; pass < 5; ++pass) {
+            double work = 0;
+            for (int b = 0; b < B.n; ++b) work += (double)np * ((N + (32 >> lqs[b]) - 1) / (32 >> lqs[b])) * cb[b];
+            bool split = false;
+            for (int b = 0; b < B.n; ++b)
+                if (cb[b] > 0.8 * work / slots && lqs[b] < 5) {
+                    ++lqs[b];
+                    cb[b] = task_cost(B, b, k, st, 1 << lqs[b], pl->kc);
+                    split = true;
+                }
+            if (!split) break;
+        }
+    }
     for (int pk = 0; pk < np; ++pk)
         for (int b = 0; b < B.n; ++b) {
-            const int lq = lanes_log2(t, pl->slice, B.l[b]);
+            const int lq = lqs[b];
             const int G = 32 >> lq;
             const int ngroup = (N + G - 1) / G;
-            double c = task_cost(B, b, k, st, 1 << lq, pl->kc);
+            const double c = cb[b];
             for (int g = 0; g < ngroup; ++g) {
                 tasks.push_back(make_int2(pk * B.n + b, g | (lq << 16)));
                 cost.push_back(c);

@@ -51,8 +51,11 @@ def test_database_matches_one_run(dk, setup, chunk):
     dst = dk.stats()
     assert np.array_equal(dres.view(np.int32), res.view(np.int32))
     assert np.array_equal(dxyz, xyz)
-    for key in ("candidates", "atom_updates", "pair_bounds", "bump_pairs", "pose_reps_skipped", "lookups_skipped"):
+    for key in ("candidates", "pair_bounds", "bump_pairs", "pose_reps_skipped"):
         assert dst[key] == st[key], key
+    # lookups left out by the gate depend on which poses share a warp, which a chunk's own launch may
+    # arrange differently (heavy ligands spread over more lanes); lookups made plus left out do not
+    assert dst["atom_updates"] + dst["lookups_skipped"] == st["atom_updates"] + st["lookups_skipped"]
     assert dst["sweep_ms"] == -1.0
 
 
