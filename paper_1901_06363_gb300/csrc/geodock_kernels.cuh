@@ -534,13 +534,20 @@ __device__ __forceinline__ void score_atoms(const PocketDev& pd, const uint16_t*
         for (int jb = 0; jb < KC; jb += BLK) {
             if ((need >> jb) & ((1ull << BLK) - 1ull)) {
 #pragma unroll
-                for (int j = jb; j < jb + BLK && j < KC; ++j) {
-                    const float2 c = angle_at(cst, j);
+                for (int j = jb; j < jb + BLK && j < KC; j += 2) {
+                    // two candidates per packed multiply-add (the roundings of place)
+                    const float4 cc = cst[j >> 1];
+                    const float2 c2 = make_float2(cc.x, cc.y), s2 = make_float2(cc.z, cc.w);
 #pragma unroll
                     for (int a = 0; a < NA; ++a) {
-                        bool in;
-                        acc[j] += term_tri<CLIP>(pd, place(s[a], c.x, c.y), &in);
-                        if (CLIP && !in) box |= 1ull << j;
+                        const float2 tx = __ffma2_rn(s2, dup2(s[a].w.x), __ffma2_rn(c2, dup2(s[a].u.x), dup2(s[a].a.x)));
+                        const float2 ty = __ffma2_rn(s2, dup2(s[a].w.y), __ffma2_rn(c2, dup2(s[a].u.y), dup2(s[a].a.y)));
+                        const float2 tz = __ffma2_rn(s2, dup2(s[a].w.z), __ffma2_rn(c2, dup2(s[a].u.z), dup2(s[a].a.z)));
+                        bool in0, in1;
+                        acc[j] += term_tri<CLIP>(pd, make_float3(tx.x, ty.x, tz.x), &in0);
+                        acc[j + 1] += term_tri<CLIP>(pd, make_float3(tx.y, ty.y, tz.y), &in1);
+                        if (CLIP && !in0) box |= 1ull << j;
+                        if (CLIP && !in1) box |= 2ull << j;
                     }
                 }
             }
