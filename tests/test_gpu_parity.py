@@ -123,6 +123,34 @@ def test_knob_variants(dk, variant):
     trace_parity(dk, pk, b, kn)
 
 
+def test_heavy_ligand_split_keeps_results(dk):
+    """With the nearest-voxel score a batch's plan may give a ligand more lanes per pose than the tile (the
+    heaviest ligands of a batch, every ligand of a small one), and the poses still working take over the
+    lanes of converged ones; neither changes a result: the default plan, a forced 2 lanes per pose and the
+    traced run (which never remaps) agree bit for bit, as do the work counts that do not depend on which
+    poses share a warp."""
+    pk = synth.pocket(8, 64, 0.5, C.ELLIPSOID)
+    l, t = synth.ligand_sizes(41, 12, 0, [16, 64, 2, 12])
+    b = synth.ligand_batch(41, l, t)
+    kn = C.knobs(n_poses=24, hp_step=15.0, lp_step=15.0, repetitions=4, seed=6)
+    pid = dk.init_pocket(pk)
+    bid = dk.upload_ligands(b)
+    res, xyz = dk.run(bid, [pid], kn, b.n, _natoms(b))
+    st = dk.stats()
+    dk.set_tile(2, 0, 0)
+    res2, xyz2 = dk.run(bid, [pid], kn, b.n, _natoms(b))
+    st2 = dk.stats()
+    dk.set_tile(0, 0, 0)
+    assert np.array_equal(res.view(np.int32), res2.view(np.int32))
+    assert np.array_equal(xyz, xyz2)
+    for key in ("candidates", "pair_bounds", "bump_pairs", "pose_reps_skipped"):
+        assert st[key] == st2[key], key
+    assert st["atom_updates"] + st["lookups_skipped"] == st2["atom_updates"] + st2["lookups_skipped"]
+    g = dk.run_trace(bid, pid, kn, b)
+    assert np.array_equal(res.view(np.int32), g["result"].view(np.int32))
+    dk.release_batch(bid)
+
+
 @pytest.mark.parametrize("clip", [1, 0])
 def test_trilinear_non_cubic_grid(dk, clip):
     """Trilinear score on a 37 x 23 x 19 grid (h = 0.4 A, random probe points): the corner texture's three
